@@ -1,0 +1,300 @@
+"""CPU oracle for the SMASH H^2 path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``smash_oracle.c``, a plain
+serial C implementation written from the paper, through ctypes.  It shares no
+code with the CUDA library and never imports it.
+
+Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
+  dense product ............ pinned (numpy/scipy restatement, brute force)
+  bounding cube / Morton ... pinned (per-point brute-force cell check)
+  tree ..................... pinned (partition invariants, brute force)
+  admissibility / lists .... pinned (exact cover, float geometry, perfect-tree counts)
+  Lagrange basis ........... pinned (polynomial reproduction, (3.1))
+  compr / SRRQR ............ pinned (ID identity rows, |G| <= f, Lemma 4.1,
+                             singular-value bounds vs dense SVD, scipy QRCP)
+  H^2 matvec ............... pinned (dense on small/trivial trees, symmetry,
+                             telescoping form (3.21)-(3.26) on perfect trees,
+                             error falling with the order)
+  parameter heuristic ...... pinned (the three worked values of Section 6.1)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "smash_oracle.c")
+_OUT = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KERNEL_LOG, KERNEL_INVR, KERNEL_YUKAWA, KERNEL_CAUCHY = 0, 1, 2, 3
+
+_Q = dict(nx=0, ny=1, L=2, nnodes=3, nadm=4, nnear=5, same=6, skel_row=7, rest_row=8,
+          g_row=9, skel_col=10, rest_col=11, g_col=12, r=13, swaps_row=14, swaps_col=15,
+          badswap=16)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) into oracle/_build."""
+    os.makedirs(_OUT, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = C.CDLL(_LIB_PATH)
+        P = C.c_void_p
+        i64, i32, dbl = C.c_int64, C.c_int, C.c_double
+        lib.orc_build.restype = P
+        lib.orc_build.argtypes = [P, i64, P, i64, i32, i32, i32, i32, dbl, dbl, dbl]
+        lib.orc_free.argtypes = [P]
+        lib.orc_free.restype = None
+        lib.orc_matvec.argtypes = [P, P, P, i32]
+        lib.orc_dense_rows.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, i64, P]
+        lib.orc_dense_rows.restype = None
+        lib.orc_query.restype = i64
+        lib.orc_query.argtypes = [P, i32]
+        lib.orc_kernel.restype = dbl
+        lib.orc_kernel.argtypes = [i32, i32, P, P]
+        lib.orc_suggest_rank.restype = i32
+        lib.orc_suggest_rank.argtypes = [dbl, dbl]
+        lib.orc_bits_per_dim.restype = i32
+        lib.orc_bits_per_dim.argtypes = [i32]
+        lib.orc_bounding_cube.argtypes = [P, i64, P, i64, i32, P, P]
+        lib.orc_bounding_cube.restype = None
+        lib.orc_morton_keys.argtypes = [P, i64, i32, P, dbl, P]
+        lib.orc_morton_keys.restype = None
+        lib.orc_admissible.restype = i32
+        lib.orc_admissible.argtypes = [i32, i32, P, i32, P, dbl]
+        lib.orc_chebyshev.argtypes = [i32, P]
+        lib.orc_chebyshev.restype = None
+        lib.orc_lagrange.restype = dbl
+        lib.orc_lagrange.argtypes = [i32, P, i32, dbl]
+        lib.orc_basis_t.argtypes = [i32, i32, P, P, dbl, i32, P, P, i32, P]
+        lib.orc_basis_t.restype = None
+        lib.orc_compr.restype = i32
+        lib.orc_compr.argtypes = [P, i32, i32, dbl, dbl, P, P, P, P]
+        lib.orc_export_geometry.argtypes = [P, P, P, P, P, P, P]
+        lib.orc_export_geometry.restype = None
+        lib.orc_export_nodes.argtypes = [P] * 12
+        lib.orc_export_nodes.restype = None
+        lib.orc_export_lists.argtypes = [P] * 5
+        lib.orc_export_lists.restype = None
+        lib.orc_export_comp.argtypes = [P, i32, P, P, P, P, P]
+        lib.orc_export_comp.restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# building blocks (each a step of the paper, exposed for the pins)
+# --------------------------------------------------------------------------
+
+def kernel(kid: int, x, y) -> float:
+    """kappa(x, y) with value 0 at coincident points ((2.1) with d_x = 0)."""
+    x, y = _f64(x).ravel(), _f64(y).ravel()
+    return _load().orc_kernel(kid, len(x), _ptr(x), _ptr(y))
+
+
+def dense_rows(x, kid: int, q, rows=None, y=None) -> np.ndarray:
+    """Brute-force rows of A q with Neumaier summation; A_ij = kappa(x_i, y_j)."""
+    x = _f64(x)
+    y = x if y is None else _f64(y)
+    q = _f64(q)
+    if q.ndim == 1:
+        q = q[:, None]
+    nrhs = q.shape[1]
+    rows = np.arange(len(x), dtype=np.int64) if rows is None else np.ascontiguousarray(rows, np.int64)
+    out = np.empty((len(rows), nrhs))
+    _load().orc_dense_rows(_ptr(x), len(x), _ptr(y), len(y), x.shape[1], kid, _ptr(q), nrhs,
+                           _ptr(rows), len(rows), _ptr(out))
+    return out
+
+
+def suggest_rank(eps: float, tau: float) -> int:
+    """The farfield rank heuristic of Section 6.1."""
+    return _load().orc_suggest_rank(eps, tau)
+
+
+def bits_per_dim(d: int) -> int:
+    return _load().orc_bits_per_dim(d)
+
+
+def bounding_cube(x, y=None):
+    x = _f64(x)
+    d = x.shape[1]
+    lo = np.zeros(3)
+    s = np.zeros(1)
+    yy = None if y is None else _f64(y)
+    _load().orc_bounding_cube(_ptr(x), len(x), _ptr(yy), 0 if yy is None else len(yy), d,
+                              _ptr(lo), _ptr(s))
+    return lo[:d].copy(), float(s[0])
+
+
+def morton_keys(pts, lo, s) -> np.ndarray:
+    pts = _f64(pts)
+    lo = _f64(np.concatenate([np.asarray(lo, np.float64), np.zeros(3)])[:3])
+    keys = np.empty(len(pts), dtype=np.uint64)
+    _load().orc_morton_keys(_ptr(pts), len(pts), pts.shape[1], _ptr(lo), float(s), _ptr(keys))
+    return keys
+
+
+def admissible(d: int, li: int, ci, lj: int, cj, tau: float) -> bool:
+    ci = np.ascontiguousarray(list(ci) + [0] * (3 - len(ci)), dtype=np.uint64)
+    cj = np.ascontiguousarray(list(cj) + [0] * (3 - len(cj)), dtype=np.uint64)
+    return bool(_load().orc_admissible(d, li, _ptr(ci), lj, _ptr(cj), tau))
+
+
+def chebyshev(p: int) -> np.ndarray:
+    t = np.empty(p)
+    _load().orc_chebyshev(p, _ptr(t))
+    return t
+
+
+def lagrange(p: int, m: int, t: float, anchors=None) -> float:
+    anchors = chebyshev(p) if anchors is None else _f64(anchors)
+    return _load().orc_lagrange(p, _ptr(anchors), m, float(t))
+
+
+def basis_t(pts, p: int, lo, s: float, level: int, cell, anchors=None) -> np.ndarray:
+    """U^^T (r x npts) of the cell (level, cell) of the cube [lo, lo+s]^d."""
+    pts = _f64(pts)
+    d = pts.shape[1]
+    anchors = chebyshev(p) if anchors is None else _f64(anchors)
+    lo3 = _f64(np.concatenate([np.asarray(lo, np.float64), np.zeros(3)])[:3])
+    cell3 = np.ascontiguousarray(list(cell) + [0] * (3 - len(cell)), dtype=np.uint64)
+    r = p ** d
+    Mt = np.empty((r, len(pts)))
+    _load().orc_basis_t(d, p, _ptr(anchors), _ptr(lo3), float(s), level, _ptr(cell3), _ptr(pts),
+                        len(pts), _ptr(Mt))
+    return Mt
+
+
+def compr(Mt, tol: float, f: float = 2.0):
+    """Strong RRQR / ID of the r x m matrix Mt (Theorem 2.4, (2.11)).
+
+    Returns (perm, k, A, nswaps): perm[:k] are the selected columns, perm[k:]
+    the others, A = R11^{-1} R12 (k x (m-k)), so that in exact arithmetic
+    Mt[:, perm[k:]] ~= Mt[:, perm[:k]] @ A."""
+    Mt = _f64(Mt)
+    r, m = Mt.shape
+    perm = np.empty(m, dtype=np.int32)
+    kmax = min(r, m)
+    A = np.zeros(max(kmax * max(m - 1, 0) + 1, 1))
+    k = C.c_int(0)
+    ns = C.c_int(0)
+    _load().orc_compr(_ptr(Mt), r, m, tol, f, _ptr(perm), C.byref(k), _ptr(A), C.byref(ns))
+    k = k.value
+    return perm, k, A[: k * (m - k)].reshape(k, m - k).copy(), ns.value
+
+
+# --------------------------------------------------------------------------
+# the whole H^2 construction and matvec
+# --------------------------------------------------------------------------
+
+class H2:
+    """Oracle H^2 approximation of A = [kappa(x_i, y_j)] (Section 3.3.2)."""
+
+    def __init__(self, x, kernel: int, leaf: int, order: int, tol: float, y=None,
+                 tau: float = 0.7, f: float = 2.0):
+        lib = _load()
+        self.x = _f64(x)
+        self.y = None if y is None else _f64(y)
+        self.d = self.x.shape[1]
+        self.kernel, self.leaf, self.order, self.tol, self.tau, self.f = kernel, leaf, order, tol, tau, f
+        ny = 0 if self.y is None else len(self.y)
+        h = lib.orc_build(_ptr(self.x), len(self.x), _ptr(self.y), ny, self.d, kernel, leaf, order,
+                          tau, tol, f)
+        if not h:
+            raise ValueError("oracle: invalid input")
+        self._h = C.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_free(h)
+            self._h = None
+
+    def query(self, what: str) -> int:
+        return int(_load().orc_query(self._h, _Q[what]))
+
+    def matvec(self, q) -> np.ndarray:
+        q = _f64(q)
+        squeeze = q.ndim == 1
+        if squeeze:
+            q = q[:, None]
+        q = np.ascontiguousarray(q)
+        z = np.empty((self.query("nx"), q.shape[1]))
+        _load().orc_matvec(self._h, _ptr(q), _ptr(z), q.shape[1])
+        return z[:, 0] if squeeze else z
+
+    def export(self) -> dict:
+        """Every array of the representation, in the layout shared by the
+        library's smash_export (documented in include/smash.h)."""
+        lib = _load()
+        nx, ny, L, nn = (self.query(k) for k in ("nx", "ny", "L", "nnodes"))
+        nadm, nnear = self.query("nadm"), self.query("nnear")
+        e = {}
+        lo = np.zeros(3)
+        s = np.zeros(1)
+        e["permx"] = np.empty(nx, np.int64)
+        e["permy"] = np.empty(ny, np.int64)
+        e["keyx"] = np.empty(nx, np.uint64)
+        e["keyy"] = np.empty(ny, np.uint64)
+        lib.orc_export_geometry(self._h, _ptr(lo), _ptr(s), _ptr(e["permx"]), _ptr(e["permy"]),
+                                _ptr(e["keyx"]), _ptr(e["keyy"]))
+        e["lo"], e["s"] = lo[: self.d].copy(), float(s[0])
+        e["L"] = L
+        e["lvl_off"] = np.empty(L + 1, np.int64)
+        for name, dt in (("level", np.int32), ("leaf", np.int32), ("parent", np.int32),
+                         ("child0", np.int32), ("nchild", np.int32), ("rs", np.int64),
+                         ("rc", np.int64), ("cs", np.int64), ("cc", np.int64)):
+            e[name] = np.empty(nn, dt)
+        e["cell"] = np.empty((nn, 3), np.uint64)
+        lib.orc_export_nodes(self._h, _ptr(e["lvl_off"]), _ptr(e["level"]), _ptr(e["leaf"]),
+                             _ptr(e["parent"]), _ptr(e["child0"]), _ptr(e["nchild"]), _ptr(e["rs"]),
+                             _ptr(e["rc"]), _ptr(e["cs"]), _ptr(e["cc"]), _ptr(e["cell"]))
+        e["adm_ptr"] = np.empty(nn + 1, np.int64)
+        e["near_ptr"] = np.empty(nn + 1, np.int64)
+        e["adm_col"] = np.empty(nadm, np.int32)
+        e["near_col"] = np.empty(nnear, np.int32)
+        lib.orc_export_lists(self._h, _ptr(e["adm_ptr"]), _ptr(e["adm_col"]), _ptr(e["near_ptr"]),
+                             _ptr(e["near_col"]))
+        for side, tag in ((0, "row"), (1, "col")):
+            e[f"m_{tag}"] = np.empty(nn, np.int32)
+            e[f"k_{tag}"] = np.empty(nn, np.int32)
+            e[f"skel_{tag}"] = np.empty(self.query(f"skel_{tag}"), np.int64)
+            e[f"rest_{tag}"] = np.empty(self.query(f"rest_{tag}"), np.int64)
+            e[f"G_{tag}"] = np.empty(self.query(f"g_{tag}"), np.float64)
+            lib.orc_export_comp(self._h, side, _ptr(e[f"m_{tag}"]), _ptr(e[f"k_{tag}"]),
+                                _ptr(e[f"skel_{tag}"]), _ptr(e[f"rest_{tag}"]), _ptr(e[f"G_{tag}"]))
+        e["swaps_row"] = self.query("swaps_row")
+        e["badswap"] = self.query("badswap")
+        return e

@@ -1,0 +1,949 @@
+/*
+ * smash_oracle.c -- plain, slow, serial CPU oracle for the SMASH H^2 path.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this code.  It shares nothing with the CUDA library:
+ * every step is written out here from the paper (Cai, Chow, Saad, Xi,
+ * "SMASH: Structured Matrix Approximation by Separation and Hierarchy").
+ *
+ * What it computes, in the paper's order:
+ *   - dense brute force  z_i = sum_j kappa(x_i, y_j) q_j  (Neumaier-compensated),
+ *     the plain definition of A q (Sections 1.2 and 2.2);
+ *   - adaptive partitioning of the bounding cube (Section 3.1);
+ *   - admissible leaves L (3.3) and inadmissible leaves L^- (3.4) with the
+ *     well-separation test of Definition 2.1 applied to node cells (4.6);
+ *   - interpolation bases U^_i from Lagrange polynomials at Chebyshev anchors
+ *     of the node cell (2.2) and the basis choice discussed around (3.1);
+ *   - compr = strong rank-revealing QR of U^_i^T (Theorem 2.4, s = f = 2)
+ *     giving the interpolative decomposition (2.11)/(2.14);
+ *   - the bottom-up H^2 construction (3.16)-(3.20);
+ *   - the node-wise H^2 matvec of Section 3.4 (upward, coupling, downward,
+ *     near field).
+ *
+ * Readings of the paper that are not fixed by its text are applied exactly
+ * as the design notes list them: cube normalisation, Morton digit order,
+ * split iff count > leaf_size, cell-based admissibility, Chebyshev anchors
+ * of the first kind, ascending skeleton order, QR with column pivoting
+ * stopped at |R_jj| <= tol |R_00|, followed by Gu-Eisenstat swaps until
+ * max_ij (A_ij^2 + gamma_j^2 / omega_i^2) <= f^2.
+ *
+ * Compile with -ffp-contract=off: every a*b+c below is two rounded operations.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MAXP 64
+#define ORC_MAX_SWAPS 1000
+
+enum { ORC_K_LOG = 0, ORC_K_INVR = 1, ORC_K_YUKAWA = 2, ORC_K_CAUCHY = 3 };
+
+/* ------------------------------------------------------------------------ */
+/* kernels (2.1) with the diagonal value 0                                   */
+/* ------------------------------------------------------------------------ */
+
+double orc_kernel(int kid, int d, const double *x, const double *y)
+{
+    if (kid == ORC_K_CAUCHY) {
+        double t = x[0] - y[0];
+        return t == 0.0 ? 0.0 : 1.0 / t;
+    }
+    double r2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+        double t = x[a] - y[a];
+        r2 += t * t;
+    }
+    if (r2 == 0.0)
+        return 0.0;
+    double r = sqrt(r2);
+    switch (kid) {
+    case ORC_K_LOG: return log(r);
+    case ORC_K_INVR: return 1.0 / r;
+    case ORC_K_YUKAWA: return exp(-r) / r;
+    default: return 0.0;
+    }
+}
+
+/* Neumaier-compensated dense product for selected rows:
+ * out[t*nrhs+c] = sum_j kappa(x[rows[t]], y[j]) q[j*nrhs+c]. */
+void orc_dense_rows(const double *x, int64_t nx, const double *y, int64_t ny, int d, int kid,
+                    const double *q, int nrhs, const int64_t *rows, int64_t nrows, double *out)
+{
+    (void)nx;
+    double *sum = malloc(sizeof(double) * (size_t)nrhs);
+    double *comp = malloc(sizeof(double) * (size_t)nrhs);
+    for (int64_t t = 0; t < nrows; ++t) {
+        const double *xi = x + rows[t] * d;
+        for (int c = 0; c < nrhs; ++c) { sum[c] = 0.0; comp[c] = 0.0; }
+        for (int64_t j = 0; j < ny; ++j) {
+            double k = orc_kernel(kid, d, xi, y + j * d);
+            for (int c = 0; c < nrhs; ++c) {
+                double v = k * q[j * nrhs + c];
+                double s = sum[c] + v;
+                if (fabs(sum[c]) >= fabs(v))
+                    comp[c] += (sum[c] - s) + v;
+                else
+                    comp[c] += (v - s) + sum[c];
+                sum[c] = s;
+            }
+        }
+        for (int c = 0; c < nrhs; ++c)
+            out[t * nrhs + c] = sum[c] + comp[c];
+    }
+    free(sum);
+    free(comp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 6.1 parameter heuristic                                           */
+/* ------------------------------------------------------------------------ */
+
+int orc_suggest_rank(double eps, double tau)
+{
+    double v = log(eps) / log(tau);
+    if (eps < 1e-8)
+        return (int)floor(v - 20.0);
+    if (eps < 1e-6)
+        return (int)floor(v - 15.0);
+    int r = (int)floor(v - 10.0);
+    return r > 5 ? r : 5;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.1: bounding cube and Morton keys                                */
+/* ------------------------------------------------------------------------ */
+
+int orc_bits_per_dim(int d) { return d == 1 ? 62 : (d == 2 ? 31 : 21); }
+
+/* Smallest axis-aligned cube [lo, lo+s]^d holding X and Y (y may be NULL).
+ * s = largest extent times (1 + 2^-40), or 1 when all points coincide. */
+void orc_bounding_cube(const double *x, int64_t nx, const double *y, int64_t ny, int d,
+                       double *lo, double *s)
+{
+    double hi[3];
+    for (int a = 0; a < d; ++a) { lo[a] = x[a]; hi[a] = x[a]; }
+    for (int64_t i = 0; i < nx; ++i)
+        for (int a = 0; a < d; ++a) {
+            double v = x[i * d + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    if (y)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int a = 0; a < d; ++a) {
+                double v = y[i * d + a];
+                if (v < lo[a]) lo[a] = v;
+                if (v > hi[a]) hi[a] = v;
+            }
+    double ext = 0.0;
+    for (int a = 0; a < d; ++a)
+        if (hi[a] - lo[a] > ext) ext = hi[a] - lo[a];
+    *s = ext > 0.0 ? ext * (1.0 + 0x1p-40) : 1.0;
+}
+
+/* Integer cell coordinate of one coordinate value at the finest level:
+ * floor((v - lo)/s * 2^b), clamped to [0, 2^b - 1]. */
+static uint64_t orc_quantize(double v, double lo, double s, int b)
+{
+    double t = (v - lo) / s;
+    double f = floor(t * ldexp(1.0, b));
+    uint64_t top = (((uint64_t)1) << b) - 1;
+    if (!(f > 0.0))
+        return 0;
+    if (f >= ldexp(1.0, b))
+        return top;
+    uint64_t q = (uint64_t)f;
+    return q > top ? top : q;
+}
+
+/* Morton key: b digits of d bits, most significant digit first; within a
+ * digit, dimension 0 is the most significant bit. */
+uint64_t orc_morton_key(const double *pt, int d, const double *lo, double s)
+{
+    int b = orc_bits_per_dim(d);
+    uint64_t q[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a)
+        q[a] = orc_quantize(pt[a], lo[a], s, b);
+    uint64_t key = 0;
+    for (int l = 0; l < b; ++l)
+        for (int a = 0; a < d; ++a)
+            key = (key << 1) | ((q[a] >> (b - 1 - l)) & 1u);
+    return key;
+}
+
+void orc_morton_keys(const double *pts, int64_t n, int d, const double *lo, double s, uint64_t *keys)
+{
+    for (int64_t i = 0; i < n; ++i)
+        keys[i] = orc_morton_key(pts + i * d, d, lo, s);
+}
+
+typedef struct { uint64_t key; int64_t idx; } orc_kv;
+
+static int orc_kv_cmp(const void *pa, const void *pb)
+{
+    const orc_kv *a = pa, *b = pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+/* Stable sort of the points by key: perm[p] = original index at sorted position p. */
+static void orc_sort_points(const double *pts, int64_t n, int d, const double *lo, double s,
+                            int64_t *perm, uint64_t *keys_sorted, double *pts_sorted)
+{
+    orc_kv *kv = malloc(sizeof(orc_kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        kv[i].key = orc_morton_key(pts + i * d, d, lo, s);
+        kv[i].idx = i;
+    }
+    qsort(kv, (size_t)n, sizeof(orc_kv), orc_kv_cmp);
+    for (int64_t p = 0; p < n; ++p) {
+        perm[p] = kv[p].idx;
+        keys_sorted[p] = kv[p].key;
+        for (int a = 0; a < d; ++a)
+            pts_sorted[p * d + a] = pts[kv[p].idx * d + a];
+    }
+    free(kv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Definition 2.1 on cells                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Cells are dyadic cubes: a node at level l (root = 1) with integer cell
+ * coordinates c has side h_l = s 2^(1-l), centre lo + (c + 1/2) h_l and
+ * radius sqrt(d) h_l / 2 (the smallest ball around the cube).  In units of
+ * half the finer cell, u = s 2^-m with m = max(li, lj), the centres are the
+ * integers (2c+1) 2^(m-l) and the radii sqrt(d) 2^(m-l).  (2.3) squared:
+ *     d (2^(m-li) + 2^(m-lj))^2  <=  tau^2 sum_a D_a^2,
+ * D the integer centre difference.  Returns 1 when well-separated. */
+int orc_admissible(int d, int li, const uint64_t *ci, int lj, const uint64_t *cj, double tau)
+{
+    int m = li > lj ? li : lj;
+    double e = ldexp(1.0, m - li) + ldexp(1.0, m - lj);
+    double lhs = (double)d * (e * e);
+    double sum = 0.0;
+    for (int a = 0; a < d; ++a) {
+        uint64_t Ci = (2 * ci[a] + 1) << (m - li);
+        uint64_t Cj = (2 * cj[a] + 1) << (m - lj);
+        uint64_t D = Ci >= Cj ? Ci - Cj : Cj - Ci;
+        double Dd = (double)D;
+        sum = sum + Dd * Dd;
+    }
+    double tau2 = tau * tau;
+    return lhs <= tau2 * sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* (2.2): Lagrange polynomials at Chebyshev points, tensor basis             */
+/* ------------------------------------------------------------------------ */
+
+/* Chebyshev points of the first kind on [-1, 1]. */
+void orc_chebyshev(int p, double *t)
+{
+    for (int m = 0; m < p; ++m)
+        t[m] = cos((double)(2 * m + 1) * ORC_PI / (double)(2 * p));
+}
+
+/* ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n). */
+double orc_lagrange(int p, const double *anchors, int m, double t)
+{
+    double v = 1.0;
+    for (int n = 0; n < p; ++n) {
+        if (n == m) continue;
+        double num = t - anchors[n];
+        double den = anchors[m] - anchors[n];
+        v = v * (num / den);
+    }
+    return v;
+}
+
+/* Transpose of the interpolation basis of one cell, evaluated at npts points:
+ * Mt[kk * npts + c] = prod_a ell_{k_a}(t_a(x_c)), kk = (k_0 p + k_1) p + k_2
+ * (last dimension fastest), t_a = (x_a - centre_a) / (h/2) in [-1, 1].
+ * The cell: level l (root 1) with integer coordinates cell[] in the cube
+ * [lo, lo+s]^d. */
+void orc_basis_t(int d, int p, const double *anchors, const double *lo, double s, int level,
+                 const uint64_t *cell, const double *pts, int npts, double *Mt)
+{
+    double h = ldexp(s, 1 - level);
+    double half = 0.5 * h;
+    int r = 1;
+    for (int a = 0; a < d; ++a) r *= p;
+    double L[3][ORC_MAXP];
+    for (int c = 0; c < npts; ++c) {
+        for (int a = 0; a < d; ++a) {
+            double centre = lo[a] + ((double)cell[a] + 0.5) * h;
+            double t = (pts[c * d + a] - centre) / half;
+            for (int m = 0; m < p; ++m)
+                L[a][m] = orc_lagrange(p, anchors, m, t);
+        }
+        for (int kk = 0; kk < r; ++kk) {
+            int rem = kk, idx[3] = {0, 0, 0};
+            for (int a = d - 1; a >= 0; --a) { idx[a] = rem % p; rem /= p; }
+            double v = L[0][idx[0]];
+            for (int a = 1; a < d; ++a) v = v * L[a][idx[a]];
+            Mt[(size_t)kk * npts + c] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Theorem 2.4: strong rank-revealing QR and the ID (2.11)                   */
+/* ------------------------------------------------------------------------ */
+
+/* One Householder step on column j of W (r x m row-major), rows j..r-1,
+ * applied to the columns j+1..m-1.  Afterwards W[j][j] = R_jj and the
+ * entries below it are zero. */
+static void orc_householder(double *W, int r, int m, int j, double *v)
+{
+    double alpha = W[(size_t)j * m + j];
+    double sigma = 0.0;
+    for (int i = j + 1; i < r; ++i) {
+        double x = W[(size_t)i * m + j];
+        sigma = sigma + x * x;
+    }
+    if (sigma == 0.0)
+        return; /* already triangular in this column: H = I */
+    double nrm = sqrt(alpha * alpha + sigma);
+    double beta = alpha <= 0.0 ? nrm : -nrm;
+    double tau = (beta - alpha) / beta;
+    double den = alpha - beta;
+    v[j] = 1.0;
+    for (int i = j + 1; i < r; ++i)
+        v[i] = W[(size_t)i * m + j] / den;
+    for (int c = j + 1; c < m; ++c) {
+        double w = W[(size_t)j * m + c];
+        for (int i = j + 1; i < r; ++i)
+            w = w + v[i] * W[(size_t)i * m + c];
+        double tw = tau * w;
+        W[(size_t)j * m + c] = W[(size_t)j * m + c] - tw;
+        for (int i = j + 1; i < r; ++i)
+            W[(size_t)i * m + c] = W[(size_t)i * m + c] - tw * v[i];
+    }
+    W[(size_t)j * m + j] = beta;
+    for (int i = j + 1; i < r; ++i)
+        W[(size_t)i * m + j] = 0.0;
+}
+
+/* Householder QR of W (r x m).  pivot = 1: column pivoting on the largest
+ * remaining column norm (ties: lowest position), stopping before step j
+ * when |R_jj| <= tol |R_00|; returns the number of steps k.  pivot = 0:
+ * exactly ksteps steps in the given column order. */
+static int orc_qr(double *W, int r, int m, int *perm, int pivot, int ksteps, double tol,
+                  double *nrm2, double *v)
+{
+    int kmax = pivot ? (r < m ? r : m) : ksteps;
+    double r00 = 0.0;
+    for (int j = 0; j < kmax; ++j) {
+        if (pivot) {
+            for (int c = j; c < m; ++c) {
+                double s2 = 0.0;
+                for (int i = j; i < r; ++i) {
+                    double x = W[(size_t)i * m + c];
+                    s2 = s2 + x * x;
+                }
+                nrm2[c] = s2;
+            }
+            int piv = j;
+            for (int c = j + 1; c < m; ++c)
+                if (nrm2[c] > nrm2[piv]) piv = c;
+            double nrm = sqrt(nrm2[piv]);
+            if (j == 0) {
+                r00 = nrm;
+                if (nrm == 0.0) return 0;
+            } else if (nrm <= tol * r00) {
+                return j;
+            }
+            if (piv != j) {
+                for (int i = 0; i < r; ++i) {
+                    double t = W[(size_t)i * m + j];
+                    W[(size_t)i * m + j] = W[(size_t)i * m + piv];
+                    W[(size_t)i * m + piv] = t;
+                }
+                int tp = perm[j]; perm[j] = perm[piv]; perm[piv] = tp;
+            }
+        }
+        orc_householder(W, r, m, j, v);
+    }
+    return kmax;
+}
+
+/* compr (2.14) on Mt = U^_i^T (r x m, row-major; not modified).
+ * Output: perm (m entries; perm[0..k) are the selected columns = skeleton
+ * positions, perm[k..m) the rest), *k_out, A = R11^{-1} R12 (k x (m-k),
+ * row-major) and the number of Gu-Eisenstat swaps (-1 if the cap was hit).
+ * A must hold k*(m-k) doubles with k <= min(r, m). */
+int orc_compr(const double *Mt, int r, int m, double tol, double f, int *perm, int *k_out,
+              double *A, int *nswaps_out)
+{
+    double *W = malloc(sizeof(double) * (size_t)r * (size_t)(m > 0 ? m : 1));
+    double *nrm2 = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *v = malloc(sizeof(double) * (size_t)(r > 0 ? r : 1));
+    for (int c = 0; c < m; ++c) perm[c] = c;
+    memcpy(W, Mt, sizeof(double) * (size_t)r * (size_t)m);
+    int k = orc_qr(W, r, m, perm, 1, 0, tol, nrm2, v);
+    int nsw = 0;
+    int mk = m - k;
+    double *X = malloc(sizeof(double) * (size_t)(k > 0 ? k * k : 1));
+    double *rho = malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    double *g2 = malloc(sizeof(double) * (size_t)(mk > 0 ? mk : 1));
+    for (;;) {
+        if (k == 0 || mk == 0) break;
+        /* A = R11^{-1} R12 by back substitution, one column at a time */
+        for (int u = 0; u < mk; ++u)
+            for (int t = k - 1; t >= 0; --t) {
+                double s = W[(size_t)t * m + k + u];
+                for (int q = t + 1; q < k; ++q)
+                    s = s - W[(size_t)t * m + q] * A[(size_t)q * mk + u];
+                A[(size_t)t * mk + u] = s / W[(size_t)t * m + t];
+            }
+        /* X = R11^{-1}; 1/omega_t^2 = squared norm of row t of X */
+        for (int c = 0; c < k; ++c)
+            for (int t = k - 1; t >= 0; --t) {
+                double s = (t == c) ? 1.0 : 0.0;
+                for (int q = t + 1; q < k; ++q)
+                    s = s - W[(size_t)t * m + q] * X[(size_t)q * k + c];
+                X[(size_t)t * k + c] = s / W[(size_t)t * m + t];
+            }
+        for (int t = 0; t < k; ++t) {
+            double s = 0.0;
+            for (int c = 0; c < k; ++c) {
+                double x = X[(size_t)t * k + c];
+                s = s + x * x;
+            }
+            rho[t] = s;
+        }
+        /* gamma_u^2 = squared norm of column u of R22 */
+        for (int u = 0; u < mk; ++u) {
+            double s = 0.0;
+            for (int i = k; i < r; ++i) {
+                double x = W[(size_t)i * m + k + u];
+                s = s + x * x;
+            }
+            g2[u] = s;
+        }
+        double best = -1.0;
+        int bt = 0, bu = 0;
+        for (int t = 0; t < k; ++t)
+            for (int u = 0; u < mk; ++u) {
+                double a = A[(size_t)t * mk + u];
+                double val = a * a + g2[u] * rho[t];
+                if (val > best) { best = val; bt = t; bu = u; }
+            }
+        if (best <= f * f) break;
+        if (nsw >= ORC_MAX_SWAPS) { nsw = -1; break; }
+        int tp = perm[bt]; perm[bt] = perm[k + bu]; perm[k + bu] = tp;
+        ++nsw;
+        /* rebuild the permuted matrix and re-triangularise its first k columns */
+        for (int i = 0; i < r; ++i)
+            for (int c = 0; c < m; ++c)
+                W[(size_t)i * m + c] = Mt[(size_t)i * m + perm[c]];
+        orc_qr(W, r, m, perm, 0, k, tol, nrm2, v);
+    }
+    *k_out = k;
+    *nswaps_out = nsw;
+    free(W); free(nrm2); free(v); free(X); free(rho); free(g2);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The H^2 representation                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int m, k, nswaps;
+    int64_t *ibar;    /* m working-set point indices (sorted positions) */
+    int64_t *skel;    /* k skeleton indices, ascending */
+    int64_t *rest;    /* m-k others, ascending */
+    int32_t *skel_loc, *rest_loc; /* their positions in ibar */
+    double *G;        /* (m-k) x k, row-major: rows = rest, columns = skel */
+} orc_comp;
+
+typedef struct {
+    int level, leaf, parent, child0, nchild;
+    int64_t rs, rc, cs, cc;
+    uint64_t cell[3];
+} orc_node;
+
+typedef struct orc_h2 {
+    int d, kid, leaf, p, r, same, b;
+    double tau, tol, f;
+    int64_t nx, ny;
+    double lo[3], s;
+    double anchors[ORC_MAXP];
+    int64_t *permx, *permy;
+    uint64_t *keyx, *keyy;
+    double *xs, *ys;
+    int L;
+    int64_t *lvl_off; /* nodes of level l (1-based) are gids [lvl_off[l-1], lvl_off[l]) */
+    int nnodes, cap;
+    orc_node *nodes;
+    int64_t *adm_ptr, *near_ptr;
+    int32_t *adm_col, *near_col;
+    int64_t nadm, nnear;
+    orc_comp *rowc, *colc;
+} orc_h2;
+
+/* growable pair list */
+typedef struct { uint64_t *v; int64_t n, cap; } orc_pairs;
+
+static void orc_pairs_push(orc_pairs *p, int i, int j)
+{
+    if (p->n == p->cap) {
+        p->cap = p->cap ? 2 * p->cap : 1024;
+        p->v = realloc(p->v, sizeof(uint64_t) * (size_t)p->cap);
+    }
+    p->v[p->n++] = ((uint64_t)(uint32_t)i << 32) | (uint32_t)j;
+}
+
+static int orc_u64_cmp(const void *pa, const void *pb)
+{
+    uint64_t a = *(const uint64_t *)pa, b = *(const uint64_t *)pb;
+    return a < b ? -1 : (a > b);
+}
+
+static int orc_new_node(orc_h2 *h)
+{
+    if (h->nnodes == h->cap) {
+        h->cap = h->cap ? 2 * h->cap : 256;
+        h->nodes = realloc(h->nodes, sizeof(orc_node) * (size_t)h->cap);
+    }
+    memset(&h->nodes[h->nnodes], 0, sizeof(orc_node));
+    return h->nnodes++;
+}
+
+/* digit of a key that selects the child of a level-l node */
+static int orc_digit(uint64_t key, int d, int b, int l)
+{
+    return (int)((key >> (d * (b - l))) & ((1u << d) - 1));
+}
+
+/* Section 3.1: level-by-level bisection of every box with more than leaf
+ * points (rows or columns) along all d axes; empty boxes are dropped. */
+static void orc_build_tree(orc_h2 *h)
+{
+    int d = h->d, b = h->b;
+    h->lvl_off = malloc(sizeof(int64_t) * (size_t)(b + 3));
+    int root = orc_new_node(h);
+    orc_node *rt = &h->nodes[root];
+    rt->level = 1; rt->parent = -1; rt->child0 = -1;
+    rt->rs = 0; rt->rc = h->nx; rt->cs = 0; rt->cc = h->ny;
+    int64_t big = rt->rc > rt->cc ? rt->rc : rt->cc;
+    rt->leaf = !(big > h->leaf && 1 <= b);
+    h->lvl_off[0] = 0;
+    h->lvl_off[1] = 1;
+    int l = 1;
+    for (;;) {
+        int64_t first = h->lvl_off[l - 1], last = h->lvl_off[l];
+        for (int64_t g = first; g < last; ++g) {
+            if (h->nodes[g].leaf) continue;
+            int64_t rcur = h->nodes[g].rs, rend = h->nodes[g].rs + h->nodes[g].rc;
+            int64_t ccur = h->nodes[g].cs, cend = h->nodes[g].cs + h->nodes[g].cc;
+            h->nodes[g].child0 = -1;
+            h->nodes[g].nchild = 0;
+            for (int dig = 0; dig < (1 << d); ++dig) {
+                int64_t r0 = rcur, c0 = ccur;
+                while (rcur < rend && orc_digit(h->keyx[rcur], d, b, l) == dig) ++rcur;
+                while (ccur < cend && orc_digit(h->keyy[ccur], d, b, l) == dig) ++ccur;
+                if (rcur - r0 + ccur - c0 == 0) continue;
+                int c = orc_new_node(h);
+                orc_node *nd = &h->nodes[c];
+                orc_node *par = &h->nodes[g];
+                nd->level = l + 1;
+                nd->parent = (int)g;
+                nd->child0 = -1;
+                nd->rs = r0; nd->rc = rcur - r0;
+                nd->cs = c0; nd->cc = ccur - c0;
+                for (int a = 0; a < d; ++a)
+                    nd->cell[a] = 2 * par->cell[a] + (uint64_t)((dig >> (d - 1 - a)) & 1);
+                int64_t cnt = nd->rc > nd->cc ? nd->rc : nd->cc;
+                nd->leaf = !(cnt > h->leaf && (l + 1) <= b);
+                if (par->child0 < 0) par->child0 = c;
+                par->nchild++;
+            }
+        }
+        if (h->nnodes == last) break;
+        ++l;
+        h->lvl_off[l] = h->nnodes;
+    }
+    h->L = l;
+}
+
+/* (3.3)/(3.4) by dual traversal from (root, root). */
+static void orc_visit(const orc_h2 *h, int i, int j, orc_pairs *adm, orc_pairs *near)
+{
+    const orc_node *a = &h->nodes[i], *b = &h->nodes[j];
+    if (a->rc == 0 || b->cc == 0) return; /* empty block */
+    if (orc_admissible(h->d, a->level, a->cell, b->level, b->cell, h->tau)) {
+        orc_pairs_push(adm, i, j);
+    } else if (a->leaf && b->leaf) {
+        orc_pairs_push(near, i, j);
+    } else if (!a->leaf && !b->leaf) {
+        for (int ci = 0; ci < a->nchild; ++ci)
+            for (int cj = 0; cj < b->nchild; ++cj)
+                orc_visit(h, a->child0 + ci, b->child0 + cj, adm, near);
+    } else if (a->leaf) {
+        for (int cj = 0; cj < b->nchild; ++cj)
+            orc_visit(h, i, b->child0 + cj, adm, near);
+    } else {
+        for (int ci = 0; ci < a->nchild; ++ci)
+            orc_visit(h, a->child0 + ci, j, adm, near);
+    }
+}
+
+static void orc_to_csr(int nnodes, orc_pairs *p, int64_t **ptr, int32_t **col)
+{
+    qsort(p->v, (size_t)p->n, sizeof(uint64_t), orc_u64_cmp);
+    *ptr = calloc((size_t)nnodes + 1, sizeof(int64_t));
+    *col = malloc(sizeof(int32_t) * (size_t)(p->n > 0 ? p->n : 1));
+    for (int64_t e = 0; e < p->n; ++e) {
+        (*ptr)[(p->v[e] >> 32) + 1]++;
+        (*col)[e] = (int32_t)(p->v[e] & 0xffffffffu);
+    }
+    for (int g = 0; g < nnodes; ++g) (*ptr)[g + 1] += (*ptr)[g];
+}
+
+/* compr (3.16) on one node and one side; writes the canonical form. */
+static void orc_compress_node(orc_h2 *h, int g, int side)
+{
+    orc_node *nd = &h->nodes[g];
+    orc_comp *cp = side == 0 ? &h->rowc[g] : &h->colc[g];
+    const double *pts = side == 0 ? h->xs : h->ys;
+    int d = h->d, r = h->r;
+    /* working set (3.6)/(3.18) */
+    int m;
+    if (nd->leaf) {
+        m = (int)(side == 0 ? nd->rc : nd->cc);
+        int64_t st = side == 0 ? nd->rs : nd->cs;
+        cp->ibar = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        for (int c = 0; c < m; ++c) cp->ibar[c] = st + c;
+    } else {
+        m = 0;
+        for (int c = 0; c < nd->nchild; ++c)
+            m += (side == 0 ? h->rowc : h->colc)[nd->child0 + c].k;
+        cp->ibar = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        int pos = 0;
+        for (int c = 0; c < nd->nchild; ++c) {
+            orc_comp *ch = &(side == 0 ? h->rowc : h->colc)[nd->child0 + c];
+            for (int t = 0; t < ch->k; ++t) cp->ibar[pos++] = ch->skel[t];
+        }
+    }
+    cp->m = m;
+    if (m == 0) {
+        cp->k = 0;
+        return;
+    }
+    double *P = malloc(sizeof(double) * (size_t)m * (size_t)d);
+    for (int c = 0; c < m; ++c)
+        for (int a = 0; a < d; ++a) P[c * d + a] = pts[cp->ibar[c] * d + a];
+    double *Mt = malloc(sizeof(double) * (size_t)r * (size_t)m);
+    orc_basis_t(d, h->p, h->anchors, h->lo, h->s, nd->level, nd->cell, P, m, Mt);
+    int *perm = malloc(sizeof(int) * (size_t)m);
+    int kmax = r < m ? r : m;
+    double *A = malloc(sizeof(double) * (size_t)(kmax * (m - 1) + 1));
+    int k, nsw;
+    orc_compr(Mt, r, m, h->tol, h->f, perm, &k, A, &nsw);
+    cp->k = k;
+    cp->nswaps = nsw;
+    /* canonical form: skeleton and rest each in ascending position order */
+    int *sel = calloc((size_t)m, sizeof(int));
+    for (int t = 0; t < k; ++t) sel[perm[t]] = 1;
+    int *rank = malloc(sizeof(int) * (size_t)m); /* position -> sorted index */
+    int ns = 0, nr = 0;
+    for (int pos = 0; pos < m; ++pos) rank[pos] = sel[pos] ? ns++ : nr++;
+    cp->skel = malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest = malloc(sizeof(int64_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->skel_loc = malloc(sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest_loc = malloc(sizeof(int32_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->G = malloc(sizeof(double) * (size_t)((m - k) * k > 0 ? (m - k) * k : 1));
+    for (int pos = 0; pos < m; ++pos) {
+        if (sel[pos]) { cp->skel[rank[pos]] = cp->ibar[pos]; cp->skel_loc[rank[pos]] = pos; }
+        else { cp->rest[rank[pos]] = cp->ibar[pos]; cp->rest_loc[rank[pos]] = pos; }
+    }
+    int mk = m - k;
+    for (int t = 0; t < k; ++t)
+        for (int u = 0; u < mk; ++u)
+            cp->G[(size_t)rank[perm[k + u]] * k + rank[perm[t]]] = A[(size_t)t * mk + u];
+    free(P); free(Mt); free(perm); free(A); free(sel); free(rank);
+}
+
+void orc_free(orc_h2 *h);
+
+/* Build: returns NULL on invalid input.  y == NULL means Y = X. */
+orc_h2 *orc_build(const double *x, int64_t nx, const double *y, int64_t ny, int d, int kid,
+                  int leaf, int p, double tau, double tol, double f)
+{
+    if (d < 1 || d > 3 || nx < 1 || leaf < 1 || p < 1 || p > ORC_MAXP || !(tol > 0.0) ||
+        !(tau > 0.0 && tau < 1.0) || !(f > 1.0))
+        return NULL;
+    if (kid < 0 || kid > 3 || (kid == ORC_K_CAUCHY && d != 1)) return NULL;
+    if (y && ny < 1) return NULL;
+    for (int64_t i = 0; i < nx * d; ++i) if (!isfinite(x[i])) return NULL;
+    if (y) for (int64_t i = 0; i < ny * d; ++i) if (!isfinite(y[i])) return NULL;
+    orc_h2 *h = calloc(1, sizeof(orc_h2));
+    h->d = d; h->kid = kid; h->leaf = leaf; h->p = p; h->tau = tau; h->tol = tol; h->f = f;
+    h->r = 1;
+    for (int a = 0; a < d; ++a) h->r *= p;
+    h->same = (y == NULL);
+    h->nx = nx; h->ny = y ? ny : nx;
+    h->b = orc_bits_per_dim(d);
+    orc_chebyshev(p, h->anchors);
+    orc_bounding_cube(x, nx, y, ny, d, h->lo, &h->s);
+    h->permx = malloc(sizeof(int64_t) * (size_t)nx);
+    h->keyx = malloc(sizeof(uint64_t) * (size_t)nx);
+    h->xs = malloc(sizeof(double) * (size_t)nx * d);
+    orc_sort_points(x, nx, d, h->lo, h->s, h->permx, h->keyx, h->xs);
+    if (h->same) {
+        h->permy = h->permx; h->keyy = h->keyx; h->ys = h->xs;
+    } else {
+        h->permy = malloc(sizeof(int64_t) * (size_t)ny);
+        h->keyy = malloc(sizeof(uint64_t) * (size_t)ny);
+        h->ys = malloc(sizeof(double) * (size_t)ny * d);
+        orc_sort_points(y, ny, d, h->lo, h->s, h->permy, h->keyy, h->ys);
+    }
+    orc_build_tree(h);
+    orc_pairs adm = {0}, near = {0};
+    orc_visit(h, 0, 0, &adm, &near);
+    h->nadm = adm.n; h->nnear = near.n;
+    orc_to_csr(h->nnodes, &adm, &h->adm_ptr, &h->adm_col);
+    orc_to_csr(h->nnodes, &near, &h->near_ptr, &h->near_col);
+    free(adm.v); free(near.v);
+    h->rowc = calloc((size_t)h->nnodes, sizeof(orc_comp));
+    h->colc = h->same ? h->rowc : calloc((size_t)h->nnodes, sizeof(orc_comp));
+    /* (3.16)-(3.18): levels L..2, bottom-up */
+    for (int l = h->L; l >= 2; --l)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            orc_compress_node(h, (int)g, 0);
+            if (!h->same) orc_compress_node(h, (int)g, 1);
+        }
+    return h;
+}
+
+static void orc_free_comp(orc_comp *c, int n)
+{
+    if (!c) return;
+    for (int g = 0; g < n; ++g) {
+        free(c[g].ibar); free(c[g].skel); free(c[g].rest);
+        free(c[g].skel_loc); free(c[g].rest_loc); free(c[g].G);
+    }
+    free(c);
+}
+
+void orc_free(orc_h2 *h)
+{
+    if (!h) return;
+    if (!h->same) { free(h->permy); free(h->keyy); free(h->ys); orc_free_comp(h->colc, h->nnodes); }
+    free(h->permx); free(h->keyx); free(h->xs);
+    orc_free_comp(h->rowc, h->nnodes);
+    free(h->lvl_off); free(h->nodes);
+    free(h->adm_ptr); free(h->adm_col); free(h->near_ptr); free(h->near_col);
+    free(h);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.4: node-wise H^2 matvec, z = A^ q (q: ny x nrhs, z: nx x nrhs)   */
+/* ------------------------------------------------------------------------ */
+
+int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
+{
+    int d = h->d;
+    int64_t nx = h->nx, ny = h->ny;
+    double *qs = malloc(sizeof(double) * (size_t)ny * nrhs);
+    double *zs = calloc((size_t)nx * nrhs, sizeof(double));
+    for (int64_t pnt = 0; pnt < ny; ++pnt)
+        for (int c = 0; c < nrhs; ++c) qs[pnt * nrhs + c] = q[h->permy[pnt] * nrhs + c];
+    double **qhat = calloc((size_t)h->nnodes, sizeof(double *));
+    double **zhat = calloc((size_t)h->nnodes, sizeof(double *));
+    /* step 1: upward pass, q^_i = V_i^T q|_i at leaves, sum_c W_c^T q^_c above */
+    for (int l = h->L; l >= 2; --l)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            const orc_node *nd = &h->nodes[g];
+            const orc_comp *cp = &h->colc[g];
+            int m = cp->m, k = cp->k;
+            double *in = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * nrhs);
+            if (nd->leaf) {
+                memcpy(in, qs + nd->cs * nrhs, sizeof(double) * (size_t)m * nrhs);
+            } else {
+                int pos = 0;
+                for (int c = 0; c < nd->nchild; ++c) {
+                    int kc = h->colc[nd->child0 + c].k;
+                    memcpy(in + (size_t)pos * nrhs, qhat[nd->child0 + c], sizeof(double) * (size_t)kc * nrhs);
+                    pos += kc;
+                }
+            }
+            qhat[g] = calloc((size_t)(k > 0 ? k : 1) * nrhs, sizeof(double));
+            for (int t = 0; t < k; ++t)
+                for (int c = 0; c < nrhs; ++c) {
+                    double s = in[(size_t)cp->skel_loc[t] * nrhs + c];
+                    for (int u = 0; u < m - k; ++u)
+                        s = s + cp->G[(size_t)u * k + t] * in[(size_t)cp->rest_loc[u] * nrhs + c];
+                    qhat[g][(size_t)t * nrhs + c] = s;
+                }
+            free(in);
+        }
+    /* step 2: coupling, z^_i = sum_{(i,j) in L} A|_{i^ x j^} q^_j  (3.19) */
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_comp *ci = &h->rowc[g];
+        zhat[g] = calloc((size_t)(ci->k > 0 ? ci->k : 1) * nrhs, sizeof(double));
+        for (int64_t e = h->adm_ptr[g]; e < h->adm_ptr[g + 1]; ++e) {
+            int j = h->adm_col[e];
+            const orc_comp *cj = &h->colc[j];
+            for (int a = 0; a < ci->k; ++a) {
+                const double *xa = h->xs + ci->skel[a] * d;
+                for (int bb = 0; bb < cj->k; ++bb) {
+                    double kv = orc_kernel(h->kid, d, xa, h->ys + cj->skel[bb] * d);
+                    for (int c = 0; c < nrhs; ++c)
+                        zhat[g][(size_t)a * nrhs + c] += kv * qhat[j][(size_t)bb * nrhs + c];
+                }
+            }
+        }
+    }
+    /* step 3: downward pass, z^_c += R_c z^_i, and z|_i = U_i z^_i at leaves */
+    for (int l = 2; l <= h->L; ++l)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            const orc_node *nd = &h->nodes[g];
+            const orc_comp *cp = &h->rowc[g];
+            int m = cp->m, k = cp->k;
+            double *out = calloc((size_t)(m > 0 ? m : 1) * nrhs, sizeof(double));
+            for (int t = 0; t < k; ++t)
+                for (int c = 0; c < nrhs; ++c)
+                    out[(size_t)cp->skel_loc[t] * nrhs + c] = zhat[g][(size_t)t * nrhs + c];
+            for (int u = 0; u < m - k; ++u)
+                for (int c = 0; c < nrhs; ++c) {
+                    double s = 0.0;
+                    for (int t = 0; t < k; ++t)
+                        s = s + cp->G[(size_t)u * k + t] * zhat[g][(size_t)t * nrhs + c];
+                    out[(size_t)cp->rest_loc[u] * nrhs + c] = s;
+                }
+            if (nd->leaf) {
+                for (int64_t a = 0; a < (int64_t)m * nrhs; ++a) zs[nd->rs * nrhs + a] += out[a];
+            } else {
+                int pos = 0;
+                for (int c = 0; c < nd->nchild; ++c) {
+                    int kc = h->rowc[nd->child0 + c].k;
+                    for (int64_t a = 0; a < (int64_t)kc * nrhs; ++a)
+                        zhat[nd->child0 + c][a] += out[(size_t)pos * nrhs + a];
+                    pos += kc;
+                }
+            }
+            free(out);
+        }
+    /* near field (3.20): z|_i += A|_{i x j} q|_j for (i,j) in L^- */
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_node *ni = &h->nodes[g];
+        for (int64_t e = h->near_ptr[g]; e < h->near_ptr[g + 1]; ++e) {
+            const orc_node *nj = &h->nodes[h->near_col[e]];
+            for (int64_t a = ni->rs; a < ni->rs + ni->rc; ++a)
+                for (int64_t bb = nj->cs; bb < nj->cs + nj->cc; ++bb) {
+                    double kv = orc_kernel(h->kid, d, h->xs + a * d, h->ys + bb * d);
+                    for (int c = 0; c < nrhs; ++c) zs[a * nrhs + c] += kv * qs[bb * nrhs + c];
+                }
+        }
+    }
+    for (int64_t pnt = 0; pnt < nx; ++pnt)
+        for (int c = 0; c < nrhs; ++c) z[h->permx[pnt] * nrhs + c] = zs[pnt * nrhs + c];
+    for (int g = 0; g < h->nnodes; ++g) { free(qhat[g]); free(zhat[g]); }
+    free(qhat); free(zhat); free(qs); free(zs);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* introspection                                                             */
+/* ------------------------------------------------------------------------ */
+
+enum {
+    ORC_Q_NX = 0, ORC_Q_NY, ORC_Q_L, ORC_Q_NNODES, ORC_Q_NADM, ORC_Q_NNEAR, ORC_Q_SAME,
+    ORC_Q_SKEL_ROW, ORC_Q_REST_ROW, ORC_Q_G_ROW, ORC_Q_SKEL_COL, ORC_Q_REST_COL, ORC_Q_G_COL,
+    ORC_Q_R, ORC_Q_SWAPS_ROW, ORC_Q_SWAPS_COL, ORC_Q_BADSWAP
+};
+
+static void orc_comp_totals(const orc_comp *c, int n, int64_t *ts, int64_t *tr, int64_t *tg,
+                            int64_t *sw, int64_t *bad)
+{
+    *ts = *tr = *tg = *sw = *bad = 0;
+    for (int g = 0; g < n; ++g) {
+        *ts += c[g].k;
+        *tr += c[g].m - c[g].k;
+        *tg += (int64_t)(c[g].m - c[g].k) * c[g].k;
+        if (c[g].nswaps > 0) *sw += c[g].nswaps;
+        if (c[g].nswaps < 0) *bad += 1;
+    }
+}
+
+int64_t orc_query(const orc_h2 *h, int what)
+{
+    int64_t ts, tr, tg, sw, bad;
+    switch (what) {
+    case ORC_Q_NX: return h->nx;
+    case ORC_Q_NY: return h->ny;
+    case ORC_Q_L: return h->L;
+    case ORC_Q_NNODES: return h->nnodes;
+    case ORC_Q_NADM: return h->nadm;
+    case ORC_Q_NNEAR: return h->nnear;
+    case ORC_Q_SAME: return h->same;
+    case ORC_Q_R: return h->r;
+    default: break;
+    }
+    int col = (what == ORC_Q_SKEL_COL || what == ORC_Q_REST_COL || what == ORC_Q_G_COL ||
+               what == ORC_Q_SWAPS_COL);
+    orc_comp_totals(col ? h->colc : h->rowc, h->nnodes, &ts, &tr, &tg, &sw, &bad);
+    switch (what) {
+    case ORC_Q_SKEL_ROW: case ORC_Q_SKEL_COL: return ts;
+    case ORC_Q_REST_ROW: case ORC_Q_REST_COL: return tr;
+    case ORC_Q_G_ROW: case ORC_Q_G_COL: return tg;
+    case ORC_Q_SWAPS_ROW: case ORC_Q_SWAPS_COL: return sw;
+    case ORC_Q_BADSWAP: return bad;
+    default: return -1;
+    }
+}
+
+void orc_export_geometry(const orc_h2 *h, double *lo, double *s, int64_t *permx, int64_t *permy,
+                         uint64_t *keyx, uint64_t *keyy)
+{
+    for (int a = 0; a < h->d; ++a) lo[a] = h->lo[a];
+    *s = h->s;
+    memcpy(permx, h->permx, sizeof(int64_t) * (size_t)h->nx);
+    memcpy(permy, h->permy, sizeof(int64_t) * (size_t)h->ny);
+    memcpy(keyx, h->keyx, sizeof(uint64_t) * (size_t)h->nx);
+    memcpy(keyy, h->keyy, sizeof(uint64_t) * (size_t)h->ny);
+}
+
+void orc_export_nodes(const orc_h2 *h, int64_t *lvl_off, int32_t *level, int32_t *leaf,
+                      int32_t *parent, int32_t *child0, int32_t *nchild, int64_t *rs, int64_t *rc,
+                      int64_t *cs, int64_t *cc, uint64_t *cell)
+{
+    for (int l = 0; l <= h->L; ++l) lvl_off[l] = h->lvl_off[l];
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_node *n = &h->nodes[g];
+        level[g] = n->level; leaf[g] = n->leaf; parent[g] = n->parent;
+        child0[g] = n->leaf ? -1 : n->child0; nchild[g] = n->leaf ? 0 : n->nchild;
+        rs[g] = n->rs; rc[g] = n->rc; cs[g] = n->cs; cc[g] = n->cc;
+        for (int a = 0; a < 3; ++a) cell[g * 3 + a] = a < h->d ? n->cell[a] : 0;
+    }
+}
+
+void orc_export_lists(const orc_h2 *h, int64_t *adm_ptr, int32_t *adm_col, int64_t *near_ptr,
+                      int32_t *near_col)
+{
+    memcpy(adm_ptr, h->adm_ptr, sizeof(int64_t) * (size_t)(h->nnodes + 1));
+    memcpy(near_ptr, h->near_ptr, sizeof(int64_t) * (size_t)(h->nnodes + 1));
+    memcpy(adm_col, h->adm_col, sizeof(int32_t) * (size_t)h->nadm);
+    memcpy(near_col, h->near_col, sizeof(int32_t) * (size_t)h->nnear);
+}
+
+/* Per node in gid order: m, k, and concatenated skeleton, rest, G. */
+void orc_export_comp(const orc_h2 *h, int side, int32_t *m, int32_t *k, int64_t *skel,
+                     int64_t *rest, double *G)
+{
+    const orc_comp *c = side == 0 ? h->rowc : h->colc;
+    int64_t ps = 0, pr = 0, pg = 0;
+    for (int g = 0; g < h->nnodes; ++g) {
+        m[g] = c[g].m; k[g] = c[g].k;
+        int mk = c[g].m - c[g].k;
+        for (int t = 0; t < c[g].k; ++t) skel[ps++] = c[g].skel[t];
+        for (int u = 0; u < mk; ++u) rest[pr++] = c[g].rest[u];
+        for (int64_t e = 0; e < (int64_t)mk * c[g].k; ++e) G[pg++] = c[g].G[e];
+    }
+}

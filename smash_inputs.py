@@ -1,0 +1,159 @@
+"""Seeded synthetic point clouds and right-hand sides.
+
+This module is the only code shared by the CPU oracle tests, the GPU parity
+tests and the benchmark.  It draws random numbers and nothing else: it holds
+none of the method's arithmetic (no tree, no basis, no kernel evaluation).
+
+The workloads mirror the shapes of the paper's test problems (Section 6):
+points in the unit square/cube, points on a surface with clustered patches,
+Gaussian mixtures, and the mixed 1D Cauchy point sets of Section 6.3, where
+each y_j sits a small random offset to the right of x_j, as in (6.3).
+
+Every generator takes an explicit seed; the convention used by the tests and
+the benchmark is ``seed = config_index * 1000 + repetition``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "uniform_cube",
+    "sphere_with_caps",
+    "gaussian_mixture",
+    "cauchy_1d",
+    "jittered_grid",
+    "rhs",
+    "sample_rows",
+    "WORKLOADS",
+    "make_workload",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(int(seed))
+
+
+def uniform_cube(n: int, d: int, seed: int) -> np.ndarray:
+    """n points i.i.d. uniform in [0,1]^d, float64, shape (n, d), C order."""
+    return np.ascontiguousarray(_rng(seed).random((n, d)), dtype=np.float64)
+
+
+def sphere_with_caps(n: int, seed: int, frac_caps: float = 0.1, ncaps: int = 8,
+                     sigma: float = 0.02) -> np.ndarray:
+    """Points on the unit sphere S^2: (1-frac_caps) uniform (normalised
+    Gaussian vectors) plus frac_caps spread over ncaps clustered caps, each
+    point of cap m being normalise(c_m + sigma * N(0, I_3)) with c_m uniform
+    on S^2."""
+    g = _rng(seed)
+    n_caps = int(round(frac_caps * n))
+    n_uni = n - n_caps
+    u = g.standard_normal((n_uni, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    c = g.standard_normal((ncaps, 3))
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    which = g.integers(0, ncaps, size=n_caps)
+    v = c[which] + sigma * g.standard_normal((n_caps, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pts = np.concatenate([u, v], axis=0)
+    pts = pts[g.permutation(n)]
+    return np.ascontiguousarray(pts, dtype=np.float64)
+
+
+def gaussian_mixture(n: int, d: int, seed: int, ncomp: int = 4,
+                     sigma: float = 0.1) -> np.ndarray:
+    """n points from an equal-weight mixture of ncomp isotropic Gaussians with
+    means uniform in [0,1]^d and standard deviation sigma."""
+    g = _rng(seed)
+    means = g.random((ncomp, d))
+    which = g.integers(0, ncomp, size=n)
+    pts = means[which] + sigma * g.standard_normal((n, d))
+    return np.ascontiguousarray(pts, dtype=np.float64)
+
+
+def cauchy_1d(n: int, seed: int, offset: float = 1e-3):
+    """Section 6.3-style interleaved 1D point sets: x_i uniform in [0,1] and
+    y_j = x_j + offset * U(0,1).  Returns (x, y), each of shape (n, 1)."""
+    g = _rng(seed)
+    x = g.random((n, 1))
+    y = x + offset * g.random((n, 1))
+    return (np.ascontiguousarray(x, dtype=np.float64),
+            np.ascontiguousarray(y, dtype=np.float64))
+
+
+def jittered_grid(cells_per_dim: int, d: int, seed: int, per_cell: int = 1) -> np.ndarray:
+    """per_cell points drawn uniformly inside each cell of a regular grid with
+    cells_per_dim cells along each axis of [0,1]^d.  With cells_per_dim a
+    power of two and a leaf size that is a multiple of per_cell * 2^(d*j),
+    the adaptive tree of these points is a perfect 2^d-tree, while the random
+    positions avoid the exact ties of a regular lattice.  The first point is
+    moved to the origin and the last to (1 - 2^-40, ...), which keeps them in
+    their grid cells and makes the bounding cube exactly the unit cube."""
+    g = _rng(seed)
+    axes = [np.arange(cells_per_dim)] * d
+    corners = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, d)
+    corners = np.repeat(corners, per_cell, axis=0)
+    pts = (corners + g.random(corners.shape)) / cells_per_dim
+    # pin the bounding box to [0, 1 - 2^-40]^d so that the smallest cube
+    # around the points is [0, 1]^d and its dyadic cells are the grid cells
+    pts[0] = 0.0
+    pts[-1] = 1.0 - 2.0 ** -40
+    pts = pts[g.permutation(len(pts))]
+    return np.ascontiguousarray(pts, dtype=np.float64)
+
+
+def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
+    """n x nrhs standard normal right-hand sides, row-major float64."""
+    return np.ascontiguousarray(_rng(seed).standard_normal((n, nrhs)), dtype=np.float64)
+
+
+def sample_rows(n: int, count: int, seed: int) -> np.ndarray:
+    """A sorted sample of `count` distinct row indices out of n (all rows when
+    count >= n)."""
+    if count >= n:
+        return np.arange(n, dtype=np.int64)
+    return np.sort(_rng(seed).choice(n, size=count, replace=False)).astype(np.int64)
+
+
+# Kernel identifiers shared by convention (the C-ABI header and the oracle
+# each define their own copy of these numbers).
+KERNEL_LOG, KERNEL_INVR, KERNEL_YUKAWA, KERNEL_CAUCHY = 0, 1, 2, 3
+
+# The named workloads: point-cloud recipe plus method parameters.
+WORKLOADS = {
+    # 2D plain FP64, full dense check
+    "2d_log_4096": dict(kind="cube", n=4096, d=2, kernel=KERNEL_LOG, leaf=64, order=5,
+                        tol=1e-8, nrhs=4, index=0),
+    # 3D plain FP64, 1024 sampled rows
+    "3d_invr_65536": dict(kind="cube", n=65536, d=3, kernel=KERNEL_INVR, leaf=128, order=4,
+                          tol=1e-8, nrhs=16, index=1),
+    # the headline workload: the 3D 1/r configuration at N = 2^20
+    "3d_invr_1m": dict(kind="cube", n=1 << 20, d=3, kernel=KERNEL_INVR, leaf=128, order=4,
+                       tol=1e-8, nrhs=16, index=1),
+    # 3D mixed precision on the sphere with clustered caps
+    "sphere_yukawa_1m": dict(kind="sphere", n=1 << 20, d=3, kernel=KERNEL_YUKAWA, leaf=128,
+                             order=5, tol=1e-8, nrhs=32, index=2),
+}
+
+
+def make_workload(name: str, rep: int = 0, n: int | None = None):
+    """Points and right-hand sides of a named workload.  `n` overrides the
+    point count (same recipe, smaller or larger cloud).  Returns a dict with
+    x, y (None when Y = X), q and the method parameters."""
+    w = dict(WORKLOADS[name])
+    if n is not None:
+        w["n"] = int(n)
+    seed = w["index"] * 1000 + rep
+    if w["kind"] == "cube":
+        x = uniform_cube(w["n"], w["d"], seed)
+        y = None
+    elif w["kind"] == "sphere":
+        x = sphere_with_caps(w["n"], seed)
+        y = None
+    elif w["kind"] == "cauchy":
+        x, y = cauchy_1d(w["n"], seed)
+    else:
+        raise ValueError(w["kind"])
+    ny = w["n"] if y is None else len(y)
+    w["x"], w["y"] = x, y
+    w["q"] = rhs(ny, w["nrhs"], seed + 500)
+    return w
