@@ -1,0 +1,300 @@
+"""Benchmark: SMASH H^2 build + matvec throughput (points/s) on one GB300.
+
+A step is one pass of the whole path over one point cloud: the adaptive
+tree, the interaction lists, the per-level compression (basis + strong RRQR
+/ ID) and one H^2 matvec with nrhs right-hand sides.  The default workload is
+the 3D 1/|x-y| problem at N = 2^20 uniform points in the unit cube, leaf
+<= 128, 4 interpolation points per axis, RRQR tol 1e-8, 16 RHS, FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent replica of the
+workload (the path has no exchange step), timings are max-reduced and rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import smash_inputs as si  # noqa: E402
+
+METRIC = "build+matvec points/s, 3D 1/r N=2^20 at <=1e-8 rel err"
+UNIT = "points/s"
+CPU_SAMPLE_N = 32768      # oracle sample for cpu_baseline (same recipe, ~10-30 s of CPU work)
+REF_SAMPLE_N = 16384      # oracle sample per step of the reference arm
+FP64_FLOPS_PER_CLK_SM = 4  # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz) ~= 4 (2 DFMA per clock)
+NUM_SMS = 152
+PAIR_EVAL_FLOPS = 9        # squared distance (8) + reciprocal square root (1) per kernel entry
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_cpu_oracle(n: int, w: dict) -> dict:
+    import oracle
+    x = si.uniform_cube(n, w["d"], w["index"] * 1000 + 7)
+    q = si.rhs(n, w["nrhs"], w["index"] * 1000 + 8)
+    t0 = time.perf_counter()
+    h = oracle.H2(x, w["kernel"], w["leaf"], w["order"], w["tol"])
+    h.matvec(q)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "seconds": dt}
+
+
+def bench_reference(args, w):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        run_cpu_oracle(REF_SAMPLE_N, w)
+    t = []
+    for _ in range(args.steps):
+        t.append(run_cpu_oracle(REF_SAMPLE_N, w)["seconds"])
+    total = sum(t)
+    val = REF_SAMPLE_N * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"3d_invr uniform cube, N={REF_SAMPLE_N} sample of the N=2^20 recipe",
+                   "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": w["nrhs"]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"N={REF_SAMPLE_N} points per step, build + one {w['nrhs']}-RHS matvec"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args, w):
+    import torch
+    import paper_1705_05443_gb300 as sm
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    sm.load_library()
+    n = w["n"]
+    seed = w["index"] * 1000 + rank
+    x_np = si.uniform_cube(n, w["d"], seed)
+    q_np = si.rhs(n, w["nrhs"], seed + 500)
+    x = torch.from_numpy(x_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    z = torch.empty_like(q)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(host=False):
+        if host:
+            h = sm.smash_build_xy(xh, None, w["kernel"], w["leaf"], w["order"], w["tol"], stream=stream)
+            sm.smash_matvec_ex(h, qh, zh, sm.SMASH_PREC_F64, stream=stream)
+        else:
+            h = sm.smash_build_xy(x, None, w["kernel"], w["leaf"], w["order"], w["tol"], stream=stream)
+            sm.smash_matvec_ex(h, q, z, sm.SMASH_PREC_F64, stream=stream)
+        return h
+
+    sm.smash_set_profiling(True)
+    for _ in range(args.warmup):
+        sm.smash_free(step())
+    torch.cuda.synchronize()
+    info = None
+    coupling_ms, step_ms = [], []
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = sm.smash_launch_count()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        prof = sm.smash_last_profile(h)
+        coupling_ms.append(prof["coupling"])
+        if info is None:
+            info = sm.smash_info(h)
+            phases = prof
+        sm.smash_free(h)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    launches = sm.smash_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * n * args.steps / (tot_ms / 1e3)
+
+    # end to end through the same C ABI with pinned host buffers
+    xh = torch.from_numpy(x_np).pin_memory()
+    qh = torch.from_numpy(q_np).pin_memory()
+    zh = torch.empty(q_np.shape, dtype=torch.float64).pin_memory()
+    sm.smash_free(step(host=True))
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = step(host=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        sm.smash_free(h)
+    e2e_val = ws * n / statistics.median(e2e_t)
+    sm.smash_set_profiling(False)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak_tflops = NUM_SMS * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    nrhs = w["nrhs"]
+    cpl_flops = info["coupling_pairs"] * (2 * nrhs + PAIR_EVAL_FLOPS)
+    cpl_ms = statistics.mean(coupling_ms)
+    achieved = cpl_flops / (cpl_ms / 1e3) / 1e12
+    cpu = run_cpu_oracle(CPU_SAMPLE_N, w) if not args.no_cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3d_invr uniform cube N=2^20", "n": n, "dim": 3, "kernel": "1/|x-y|",
+                   "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
+                   "precision": "fp64", "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas{ws}"},
+        "roofline": {"bound": "alu", "kernel": "coupling (ksum_f64_kernel over L)",
+                     "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak_tflops, "traffic": None,
+                     "peak_source": f"FP64 {FP64_FLOPS_PER_CLK_SM} flop/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                                    "(nominal unit count, sampled clock)",
+                     "flops_per_launch": cpl_flops, "ms_per_launch": cpl_ms},
+        "phases_ms": phases,
+        "structure": {k: info[k] for k in ("levels", "nnodes", "nadm", "nnear", "skel_row", "g_row",
+                                           "coupling_pairs", "near_pairs", "swaps")},
+        "e2e": {"value": e2e_val, "unit": UNIT,
+                "h2d_bytes_per_step": int(x_np.nbytes + q_np.nbytes), "d2h_bytes_per_step": int(q_np.nbytes)},
+        "gpu_launches": int(launches / args.steps),
+        "clocks": clocks,
+        "wall_s": wall,
+        "peaks_file": peak_src,
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"N={CPU_SAMPLE_N} points of the same recipe, build + one "
+                                          f"{nrhs}-RHS matvec, serial C oracle"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d_invr_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = dict(si.WORKLOADS[args.workload])
+    if args.impl == "reference":
+        bench_reference(args, w)
+    else:
+        bench_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

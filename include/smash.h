@@ -1,0 +1,225 @@
+/*
+ * smash.h -- C ABI of the GB300 SMASH H^2 library (libsmash.so).
+ *
+ * SMASH (Cai, Chow, Saad, Xi): an H^2 approximation A^ of the dense kernel
+ * matrix A = [kappa(x_i, y_j)] built level by level from an adaptive tree,
+ * interpolation bases and a strong rank-revealing QR, then applied with the
+ * upward / coupling / downward / near-field passes of Section 3.4.
+ *
+ * Conventions for every entry point
+ *  - Pointers to point coordinates, right-hand sides and results may be host
+ *    or device memory; the library asks the CUDA runtime which one it is
+ *    and copies host data to and from the device itself.
+ *  - Point arrays are float64, n x dim, row-major (point i at p[i*dim]).
+ *    Right-hand sides X are float64 ny x nrhs row-major in the caller's point
+ *    order; results Y are float64 nx x nrhs row-major, overwritten.
+ *  - The caller keeps ownership of every buffer it passes.  A handle owns all
+ *    device memory of the representation until smash_free.
+ *  - A handle is immutable after the build.  smash_matvec_ex calls on
+ *    different streams may run concurrently on one handle; each allocates
+ *    its own scratch from the stream-ordered pool.
+ *  - Calls without _ex are synchronous.  No C++ exception crosses the ABI:
+ *    every failure is a status code, with a message in smash_last_error().
+ *  - Invalid input returns SMASH_EINVAL and leaves *out = NULL.  Invalid is:
+ *    dim not in {1,2,3}; n < 1; leaf_size < 1; order < 1 or order^dim > 512;
+ *    tol <= 0 or not finite; a non-finite coordinate; a kernel_id unknown or
+ *    not valid for dim (SMASH_K_CAUCHY1D needs dim == 1); nrhs < 1 or > 64.
+ */
+#ifndef SMASH_H
+#define SMASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SMASH_API __attribute__((visibility("default")))
+#else
+#define SMASH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smash_h2 *smash_handle;
+
+typedef enum {
+    SMASH_OK = 0,
+    SMASH_EINVAL = 1,   /* invalid argument */
+    SMASH_ENOMEM = 2,   /* device or host allocation failed */
+    SMASH_ECUDA = 3,    /* a CUDA runtime error (message has the detail) */
+    SMASH_ETIMEOUT = 4, /* a bounded device wait ran out */
+    SMASH_EDEPTH = 5,   /* tree depth limit exceeded */
+    SMASH_ENOTSUP = 6   /* option not supported on this device */
+} smash_status;
+
+/* Kernels kappa(x, y); kappa = 0 wherever x and y coincide ((2.1) with d_x = 0). */
+enum {
+    SMASH_K_LOG = 0,     /* log |x - y|                 */
+    SMASH_K_INVR = 1,    /* 1 / |x - y|                 */
+    SMASH_K_YUKAWA = 2,  /* exp(-|x - y|) / |x - y|     */
+    SMASH_K_CAUCHY1D = 3 /* 1 / (x - y), dim = 1, (6.1) */
+};
+
+/* Arithmetic of the matvec products (Section 3.4).  The build is FP64. */
+enum {
+    SMASH_PREC_F64 = 0  /* FP64 kernel evaluation, transfers and sums */
+};
+
+typedef struct {
+    double tau;     /* separation ratio of (2.3); default 0.7, must be in (0, 1) */
+    double f;       /* strong-RRQR bound s of Theorem 2.4; default 2, must be > 1 */
+    void *stream;   /* cudaStream_t for the build; NULL = a stream owned by the handle */
+} smash_options;
+
+/* Fills *opt with the defaults above. */
+SMASH_API void smash_default_options(smash_options *opt);
+
+/*
+ * smash_build -- H^2 construction of Section 3.3.2 with X = Y = points.
+ *
+ * Adaptive partition of the bounding cube (Section 3.1), admissible leaves
+ * L (3.3) and inadmissible leaves L^- (3.4) under Definition 2.1, then for
+ * levels L..2 the interpolation basis (2.2) of each node, compr (2.14) by
+ * strong RRQR (Theorem 2.4, f = 2) with rank cut |R_kk| <= tol |R_11|, and
+ * the nested generators (3.17)/(3.18).  Coupling and near-field blocks
+ * ((3.19)/(3.20)) are kept as index sets and evaluated on the fly.
+ *   points    n x dim float64 (host or device), not retained
+ *   kernel_id SMASH_K_*;  leaf_size: a box splits while it holds more points
+ *   order     interpolation points per axis (order^dim anchors per node)
+ *   tol       relative rank tolerance of the RRQR
+ *   out       receives the handle (NULL on failure)
+ * Synchronous.  Errors: SMASH_EINVAL, SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_build(const double *points, int dim, int64_t n, int kernel_id, int leaf_size,
+                         int order, double tol, smash_handle *out);
+
+/*
+ * smash_build_xy -- as smash_build for a rectangular A with X != Y: the tree
+ * partitions X and Y jointly (a box splits while it holds more than
+ * leaf_size points of X or of Y), and rows and columns get separate
+ * generators (P, G) and (F, H) of (3.16)/(3.17).  y == NULL means Y = X.
+ * opt == NULL means smash_default_options.
+ */
+SMASH_API smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_t ny, int dim,
+                            int kernel_id, int leaf_size, int order, double tol,
+                            const smash_options *opt, smash_handle *out);
+
+/*
+ * smash_matvec -- Y = A^ X by the node-wise algorithm of Section 3.4:
+ * upward pass (q^_i = V_i^T q, then W_c^T), coupling over L with kernel
+ * blocks on skeleton pairs, downward pass (R_c, then U_i), near field over L^-.
+ *   X  ny x nrhs float64, caller's point order (host or device)
+ *   Y  nx x nrhs float64, overwritten (host or device)
+ *   nrhs in [1, 64]
+ * Synchronous; FP64.  Errors: SMASH_EINVAL, SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_matvec(smash_handle h, const double *X, double *Y, int nrhs);
+
+/*
+ * smash_matvec_ex -- as smash_matvec with a precision mode (SMASH_PREC_*)
+ * and a cudaStream_t (NULL = the handle's stream).  Asynchronous with
+ * respect to the host when X and Y are device memory; with host buffers it
+ * returns after the result has been copied back.
+ */
+SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision,
+                             void *stream);
+
+/* Releases the handle and its device memory; NULL-safe; waits for the
+ * handle's pending work first. */
+SMASH_API void smash_free(smash_handle h);
+
+/* Sizes and statistics of a built representation. */
+typedef struct {
+    int64_t nx, ny;
+    int dim, kernel_id, leaf_size, order, r, same;
+    int levels;                 /* L; the root is level 1 */
+    int64_t nnodes, nadm, nnear, nleaves;
+    int64_t skel_row, rest_row, g_row; /* sum k, sum (m-k), sum (m-k)k over nodes */
+    int64_t skel_col, rest_col, g_col;
+    int64_t swaps;              /* Gu-Eisenstat swaps over all nodes and sides */
+    int64_t swap_cap_hits;      /* nodes whose swap loop hit its cap */
+    int64_t coupling_pairs;     /* sum over (i,j) in L of k_i k_j */
+    int64_t near_pairs;         /* sum over (i,j) in L^- of |i| |j| */
+    double lo[3], s;            /* bounding cube [lo, lo + s]^dim */
+    double tau, f, tol;
+    size_t footprint_bytes;     /* device bytes held by the handle */
+} smash_info_t;
+
+SMASH_API smash_status smash_info(smash_handle h, smash_info_t *info);
+
+/*
+ * smash_export -- host copies of the representation for inspection and
+ * parity tests.  Every pointer is caller-allocated host memory sized from
+ * smash_info (NULL skips that array).  Layout (gid = global node id, nodes
+ * ordered by level, then Morton order within the level; root gid 0):
+ *   permx[nx], permy[ny]  sorted position -> caller index
+ *   keyx[nx], keyy[ny]    Morton keys in sorted order
+ *   lvl_off[levels+1]     nodes of level l are gids [lvl_off[l-1], lvl_off[l])
+ *   level, leaf, parent, child0, nchild [nnodes]; rs, rc, cs, cc [nnodes]
+ *                         row/column point ranges in sorted order
+ *   cell[nnodes*3]        integer cell coordinates (unused axes 0)
+ *   adm_ptr[nnodes+1], adm_col[nadm]     L in CSR by row node, columns ascending
+ *   near_ptr[nnodes+1], near_col[nnear]  L^- likewise
+ *   m_*, k_*[nnodes]      working-set size |i_bar| and rank |i_hat| per node
+ *   skel_*[sum k]         skeleton point indices (sorted positions), per node
+ *                         ascending, nodes in gid order
+ *   rest_*[sum (m-k)]     the other working-set points, per node ascending
+ *   G_*[sum (m-k)k]       per node the (m-k) x k row-major matrix G of (2.11):
+ *                         rows follow rest_*, columns follow skel_*
+ * (*_col equals *_row when Y = X.)
+ */
+typedef struct {
+    int64_t *permx, *permy;
+    uint64_t *keyx, *keyy;
+    int64_t *lvl_off;
+    int32_t *level, *leaf, *parent, *child0, *nchild;
+    int64_t *rs, *rc, *cs, *cc;
+    uint64_t *cell;
+    int64_t *adm_ptr;
+    int32_t *adm_col;
+    int64_t *near_ptr;
+    int32_t *near_col;
+    int32_t *m_row, *k_row;
+    int64_t *skel_row, *rest_row;
+    double *G_row;
+    int32_t *m_col, *k_col;
+    int64_t *skel_col, *rest_col;
+    double *G_col;
+} smash_export_t;
+
+SMASH_API smash_status smash_export(smash_handle h, const smash_export_t *out);
+
+/* Device bytes held by a handle (0 for NULL). */
+SMASH_API size_t smash_footprint_bytes(smash_handle h);
+
+/* Upper estimate of the device bytes smash_build plus one smash_matvec with
+ * nrhs right-hand sides need for n uniformly spread points; used for
+ * admission before a build. */
+SMASH_API size_t smash_predict_footprint(int64_t n, int dim, int leaf_size, int order, int nrhs);
+
+/* The farfield-rank heuristic of Section 6.1 for tolerance eps and ratio tau. */
+SMASH_API int smash_suggest_rank(double eps, double tau);
+
+/* Message of the last failed call on this host thread ("" if none). */
+SMASH_API const char *smash_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+SMASH_API uint64_t smash_launch_count(void);
+
+/*
+ * Phase timing.  With profiling on, smash_build and smash_matvec_ex record
+ * CUDA events on the stream they run on around each phase;
+ * smash_last_profile copies the durations (ms) of the handle's last build
+ * and last matvec into ms[0..n) in this order and returns the count written:
+ *   build: 0 geometry (cube, keys, sort)  1 tree  2 lists  3 compression
+ *   matvec: 4 gather  5 near field  6 upward  7 coupling  8 downward  9 scatter
+ */
+SMASH_API void smash_set_profiling(int on);
+SMASH_API int smash_last_profile(smash_handle h, double *ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMASH_H */

@@ -69,6 +69,8 @@ def _load():
         lib.orc_free.argtypes = [P]
         lib.orc_free.restype = None
         lib.orc_matvec.argtypes = [P, P, P, i32]
+        lib.orc_matvec_leaves.argtypes = [P, P, P, i32, P, i64]
+        lib.orc_matvec_leaves.restype = i32
         lib.orc_dense_rows.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, i64, P]
         lib.orc_dense_rows.restype = None
         lib.orc_query.restype = i64
@@ -254,6 +256,19 @@ class H2:
         z = np.empty((self.query("nx"), q.shape[1]))
         _load().orc_matvec(self._h, _ptr(q), _ptr(z), q.shape[1])
         return z[:, 0] if squeeze else z
+
+    def matvec_leaves(self, q, leaves) -> np.ndarray:
+        """Rows of A^ q for the points of the given leaf gids (other rows NaN),
+        computed exactly as matvec() computes them."""
+        q = np.ascontiguousarray(_f64(q))
+        if q.ndim == 1:
+            q = q[:, None]
+        leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+        z = np.full((self.query("nx"), q.shape[1]), np.nan)
+        st = _load().orc_matvec_leaves(self._h, _ptr(q), _ptr(z), q.shape[1], _ptr(leaves), len(leaves))
+        if st != 0:
+            raise ValueError("matvec_leaves: not a leaf gid")
+        return z
 
     def export(self) -> dict:
         """Every array of the representation, in the layout shared by the

@@ -746,7 +746,10 @@ void orc_free(orc_h2 *h)
 /* Section 3.4: node-wise H^2 matvec, z = A^ q (q: ny x nrhs, z: nx x nrhs)   */
 /* ------------------------------------------------------------------------ */
 
-int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
+/* need == NULL: every node.  Otherwise only the nodes flagged in need get
+ * their coupling, downward and near-field work, and only the rows of the
+ * flagged leaves of z are written (the upward pass is always complete). */
+static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nrhs, const unsigned char *need)
 {
     int d = h->d;
     int64_t nx = h->nx, ny = h->ny;
@@ -787,6 +790,7 @@ int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
     for (int g = 0; g < h->nnodes; ++g) {
         const orc_comp *ci = &h->rowc[g];
         zhat[g] = calloc((size_t)(ci->k > 0 ? ci->k : 1) * nrhs, sizeof(double));
+        if (need && !need[g]) continue;
         for (int64_t e = h->adm_ptr[g]; e < h->adm_ptr[g + 1]; ++e) {
             int j = h->adm_col[e];
             const orc_comp *cj = &h->colc[j];
@@ -803,6 +807,7 @@ int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
     /* step 3: downward pass, z^_c += R_c z^_i, and z|_i = U_i z^_i at leaves */
     for (int l = 2; l <= h->L; ++l)
         for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            if (need && !need[g]) continue;
             const orc_node *nd = &h->nodes[g];
             const orc_comp *cp = &h->rowc[g];
             int m = cp->m, k = cp->k;
@@ -832,6 +837,7 @@ int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
         }
     /* near field (3.20): z|_i += A|_{i x j} q|_j for (i,j) in L^- */
     for (int g = 0; g < h->nnodes; ++g) {
+        if (need && !need[g]) continue;
         const orc_node *ni = &h->nodes[g];
         for (int64_t e = h->near_ptr[g]; e < h->near_ptr[g + 1]; ++e) {
             const orc_node *nj = &h->nodes[h->near_col[e]];
@@ -842,11 +848,42 @@ int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
                 }
         }
     }
-    for (int64_t pnt = 0; pnt < nx; ++pnt)
-        for (int c = 0; c < nrhs; ++c) z[h->permx[pnt] * nrhs + c] = zs[pnt * nrhs + c];
+    if (!need) {
+        for (int64_t pnt = 0; pnt < nx; ++pnt)
+            for (int c = 0; c < nrhs; ++c) z[h->permx[pnt] * nrhs + c] = zs[pnt * nrhs + c];
+    } else {
+        for (int g = 0; g < h->nnodes; ++g) {
+            if (!need[g] || !h->nodes[g].leaf) continue;
+            for (int64_t pnt = h->nodes[g].rs; pnt < h->nodes[g].rs + h->nodes[g].rc; ++pnt)
+                for (int c = 0; c < nrhs; ++c) z[h->permx[pnt] * nrhs + c] = zs[pnt * nrhs + c];
+        }
+    }
     for (int g = 0; g < h->nnodes; ++g) { free(qhat[g]); free(zhat[g]); }
     free(qhat); free(zhat); free(qs); free(zs);
     return 0;
+}
+
+int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
+{
+    return orc_matvec_masked(h, q, z, nrhs, NULL);
+}
+
+/* Rows of A^ q for the points of the given leaves only (gids), computed
+ * exactly as orc_matvec computes them: the full upward pass, then coupling,
+ * downward and near-field work on the leaves and their ancestors.  Rows of
+ * other points in z are left untouched. */
+int orc_matvec_leaves(const orc_h2 *h, const double *q, double *z, int nrhs, const int32_t *leaves,
+                      int64_t nleaves)
+{
+    unsigned char *need = calloc((size_t)h->nnodes, 1);
+    for (int64_t t = 0; t < nleaves; ++t) {
+        int g = leaves[t];
+        if (g < 0 || g >= h->nnodes || !h->nodes[g].leaf) { free(need); return -1; }
+        while (g >= 0) { need[g] = 1; g = h->nodes[g].parent; }
+    }
+    int st = orc_matvec_masked(h, q, z, nrhs, need);
+    free(need);
+    return st;
 }
 
 /* ------------------------------------------------------------------------ */

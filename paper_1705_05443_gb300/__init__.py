@@ -1,0 +1,306 @@
+"""Python binding of libsmash.so, the GB300 CUDA library for SMASH H^2
+matrices (construction of Section 3.3.2, matvec of Section 3.4).
+
+The functions here carry the names of the C entry points in
+``include/smash.h`` and only marshal arguments: every step of the build and of
+the matvec runs in the library's CUDA kernels.  Arrays may be torch tensors
+(CUDA or CPU) or numpy arrays; device tensors are passed to the library as
+device pointers, host arrays as host pointers.
+
+There is no CPU fallback: importing works without a GPU, but every call that
+computes needs the compiled library and a CUDA device, and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "SmashError", "smash_build", "smash_build_xy", "smash_matvec", "smash_matvec_ex", "smash_free",
+    "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
+    "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
+    "smash_last_profile", "H2Matrix", "load_library", "library_path",
+    "SMASH_K_LOG", "SMASH_K_INVR", "SMASH_K_YUKAWA", "SMASH_K_CAUCHY1D", "SMASH_PREC_F64",
+    "PROFILE_PHASES",
+]
+
+SMASH_K_LOG, SMASH_K_INVR, SMASH_K_YUKAWA, SMASH_K_CAUCHY1D = 0, 1, 2, 3
+SMASH_PREC_F64 = 0
+PROFILE_PHASES = ("geometry", "tree", "lists", "compression", "gather", "near", "upward", "coupling",
+                  "downward", "scatter")
+_STATUS = {0: "SMASH_OK", 1: "SMASH_EINVAL", 2: "SMASH_ENOMEM", 3: "SMASH_ECUDA", 4: "SMASH_ETIMEOUT",
+           5: "SMASH_EDEPTH", 6: "SMASH_ENOTSUP"}
+
+
+class SmashError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class smash_options(C.Structure):
+    _fields_ = [("tau", C.c_double), ("f", C.c_double), ("stream", C.c_void_p)]
+
+
+class smash_info_t(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("dim", C.c_int), ("kernel_id", C.c_int),
+                ("leaf_size", C.c_int), ("order", C.c_int), ("r", C.c_int), ("same", C.c_int),
+                ("levels", C.c_int), ("nnodes", C.c_int64), ("nadm", C.c_int64), ("nnear", C.c_int64),
+                ("nleaves", C.c_int64), ("skel_row", C.c_int64), ("rest_row", C.c_int64),
+                ("g_row", C.c_int64), ("skel_col", C.c_int64), ("rest_col", C.c_int64),
+                ("g_col", C.c_int64), ("swaps", C.c_int64), ("swap_cap_hits", C.c_int64),
+                ("coupling_pairs", C.c_int64), ("near_pairs", C.c_int64), ("lo", C.c_double * 3),
+                ("s", C.c_double), ("tau", C.c_double), ("f", C.c_double), ("tol", C.c_double),
+                ("footprint_bytes", C.c_size_t)]
+
+
+_EXPORT_FIELDS = ["permx", "permy", "keyx", "keyy", "lvl_off", "level", "leaf", "parent", "child0",
+                  "nchild", "rs", "rc", "cs", "cc", "cell", "adm_ptr", "adm_col", "near_ptr", "near_col",
+                  "m_row", "k_row", "skel_row", "rest_row", "G_row", "m_col", "k_col", "skel_col",
+                  "rest_col", "G_col"]
+
+
+class smash_export_t(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in _EXPORT_FIELDS]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build: bool = True):
+    """Load libsmash.so (compiling it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"the SMASH CUDA library is missing ({_build.LIB}); run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    P, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    lib.smash_default_options.argtypes = [P]
+    lib.smash_default_options.restype = None
+    lib.smash_build.argtypes = [P, i32, i64, i32, i32, i32, dbl, C.POINTER(P)]
+    lib.smash_build.restype = i32
+    lib.smash_build_xy.argtypes = [P, i64, P, i64, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
+    lib.smash_build_xy.restype = i32
+    lib.smash_matvec.argtypes = [P, P, P, i32]
+    lib.smash_matvec.restype = i32
+    lib.smash_matvec_ex.argtypes = [P, P, P, i32, i32, P]
+    lib.smash_matvec_ex.restype = i32
+    lib.smash_free.argtypes = [P]
+    lib.smash_free.restype = None
+    lib.smash_info.argtypes = [P, P]
+    lib.smash_info.restype = i32
+    lib.smash_export.argtypes = [P, P]
+    lib.smash_export.restype = i32
+    lib.smash_footprint_bytes.argtypes = [P]
+    lib.smash_footprint_bytes.restype = C.c_size_t
+    lib.smash_predict_footprint.argtypes = [i64, i32, i32, i32, i32]
+    lib.smash_predict_footprint.restype = C.c_size_t
+    lib.smash_suggest_rank.argtypes = [dbl, dbl]
+    lib.smash_suggest_rank.restype = i32
+    lib.smash_last_error.argtypes = []
+    lib.smash_last_error.restype = C.c_char_p
+    lib.smash_launch_count.argtypes = []
+    lib.smash_launch_count.restype = C.c_uint64
+    lib.smash_set_profiling.argtypes = [i32]
+    lib.smash_set_profiling.restype = None
+    lib.smash_last_profile.argtypes = [P, P, i32]
+    lib.smash_last_profile.restype = i32
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (None stays None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("expected a contiguous float64 tensor")
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.float64:
+            raise ValueError("expected a C-contiguous float64 array")
+        return C.c_void_p(a.ctypes.data)
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _rows(a) -> int:
+    return int(a.shape[0])
+
+
+def _check(st: int):
+    if st != 0:
+        raise SmashError(st, load_library(False).smash_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ entry points
+def smash_build(points, kernel_id: int, leaf_size: int, order: int, tol: float):
+    """smash_build(points, dim, n, ...) -> handle; points is n x dim float64."""
+    lib = load_library()
+    h = C.c_void_p()
+    n, dim = int(points.shape[0]), int(points.shape[1])
+    _check(lib.smash_build(_ptr(points), dim, n, kernel_id, leaf_size, order, float(tol), C.byref(h)))
+    return h
+
+
+def smash_build_xy(x, y, kernel_id: int, leaf_size: int, order: int, tol: float, tau: float = 0.7,
+                   f: float = 2.0, stream=None):
+    lib = load_library()
+    h = C.c_void_p()
+    opt = smash_options(tau, f, _stream_ptr(stream))
+    nx, dim = int(x.shape[0]), int(x.shape[1])
+    ny = 0 if y is None else int(y.shape[0])
+    _check(lib.smash_build_xy(_ptr(x), nx, _ptr(y), ny, dim, kernel_id, leaf_size, order, float(tol),
+                              C.byref(opt), C.byref(h)))
+    return h
+
+
+def smash_matvec(h, X, Y, nrhs: int | None = None):
+    lib = load_library()
+    nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check(lib.smash_matvec(h, _ptr(X), _ptr(Y), nrhs))
+    return Y
+
+
+def smash_matvec_ex(h, X, Y, precision: int = SMASH_PREC_F64, stream=None, nrhs: int | None = None):
+    lib = load_library()
+    nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check(lib.smash_matvec_ex(h, _ptr(X), _ptr(Y), nrhs, precision, _stream_ptr(stream)))
+    return Y
+
+
+def smash_free(h):
+    if h is not None and h.value:
+        load_library(False).smash_free(h)
+
+
+def smash_info(h) -> dict:
+    lib = load_library()
+    info = smash_info_t()
+    _check(lib.smash_info(h, C.byref(info)))
+    out = {name: getattr(info, name) for name, _ in smash_info_t._fields_}
+    out["lo"] = list(info.lo)
+    return out
+
+
+def smash_export(h) -> dict:
+    """Host copies of every array of the representation (layout in smash.h)."""
+    lib = load_library()
+    i = smash_info(h)
+    nx, ny, nn, L = i["nx"], i["ny"], i["nnodes"], i["levels"]
+    arrs = {
+        "permx": np.empty(nx, np.int64), "permy": np.empty(ny, np.int64),
+        "keyx": np.empty(nx, np.uint64), "keyy": np.empty(ny, np.uint64),
+        "lvl_off": np.empty(L + 1, np.int64),
+        "level": np.empty(nn, np.int32), "leaf": np.empty(nn, np.int32), "parent": np.empty(nn, np.int32),
+        "child0": np.empty(nn, np.int32), "nchild": np.empty(nn, np.int32),
+        "rs": np.empty(nn, np.int64), "rc": np.empty(nn, np.int64), "cs": np.empty(nn, np.int64),
+        "cc": np.empty(nn, np.int64), "cell": np.empty((nn, 3), np.uint64),
+        "adm_ptr": np.empty(nn + 1, np.int64), "adm_col": np.empty(i["nadm"], np.int32),
+        "near_ptr": np.empty(nn + 1, np.int64), "near_col": np.empty(i["nnear"], np.int32),
+    }
+    for tag in ("row", "col"):
+        arrs[f"m_{tag}"] = np.empty(nn, np.int32)
+        arrs[f"k_{tag}"] = np.empty(nn, np.int32)
+        arrs[f"skel_{tag}"] = np.empty(i[f"skel_{tag}"], np.int64)
+        arrs[f"rest_{tag}"] = np.empty(i[f"rest_{tag}"], np.int64)
+        arrs[f"G_{tag}"] = np.empty(i[f"g_{tag}"], np.float64)
+    ex = smash_export_t(*[C.c_void_p(arrs[name].ctypes.data) if arrs[name].size else None
+                          for name in _EXPORT_FIELDS])
+    _check(lib.smash_export(h, C.byref(ex)))
+    arrs["L"] = L
+    arrs["lo"] = np.array(i["lo"][: i["dim"]])
+    arrs["s"] = i["s"]
+    return arrs
+
+
+def smash_footprint_bytes(h) -> int:
+    return int(load_library().smash_footprint_bytes(h))
+
+
+def smash_predict_footprint(n: int, dim: int, leaf_size: int, order: int, nrhs: int) -> int:
+    return int(load_library().smash_predict_footprint(n, dim, leaf_size, order, nrhs))
+
+
+def smash_suggest_rank(eps: float, tau: float) -> int:
+    return int(load_library().smash_suggest_rank(eps, tau))
+
+
+def smash_last_error() -> str:
+    return load_library(False).smash_last_error().decode()
+
+
+def smash_launch_count() -> int:
+    return int(load_library().smash_launch_count())
+
+
+def smash_set_profiling(on: bool):
+    load_library().smash_set_profiling(1 if on else 0)
+
+
+def smash_last_profile(h) -> dict:
+    ms = np.zeros(len(PROFILE_PHASES))
+    n = load_library().smash_last_profile(h, C.c_void_p(ms.ctypes.data), len(ms))
+    return dict(zip(PROFILE_PHASES[:n], ms[:n].tolist()))
+
+
+class H2Matrix:
+    """Owning wrapper: builds on construction, frees on close/garbage collection."""
+
+    def __init__(self, x, kernel_id: int, leaf_size: int, order: int, tol: float, y=None,
+                 tau: float = 0.7, f: float = 2.0, stream=None):
+        self.nx = _rows(x)
+        self.ny = self.nx if y is None else _rows(y)
+        if y is None and tau == 0.7 and f == 2.0 and stream is None:
+            self.h = smash_build(x, kernel_id, leaf_size, order, tol)
+        else:
+            self.h = smash_build_xy(x, y, kernel_id, leaf_size, order, tol, tau, f, stream)
+
+    def matvec(self, X, Y=None, precision: int = SMASH_PREC_F64, stream=None):
+        if Y is None:
+            if hasattr(X, "new_empty"):
+                Y = X.new_empty((self.nx, X.shape[1]))
+            else:
+                Y = np.empty((self.nx, X.shape[1]))
+        if precision == SMASH_PREC_F64 and stream is None:
+            return smash_matvec(self.h, X, Y)
+        return smash_matvec_ex(self.h, X, Y, precision, stream)
+
+    def info(self) -> dict:
+        return smash_info(self.h)
+
+    def export(self) -> dict:
+        return smash_export(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            smash_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

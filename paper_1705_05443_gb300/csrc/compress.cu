@@ -1,0 +1,570 @@
+// compress.cu -- per-level batched node compression of Section 3.3.2:
+// interpolation basis (2.2) at Chebyshev anchors of the node cell, then
+// compr (2.14) = strong rank-revealing QR of U^_i^T (Theorem 2.4) giving the
+// interpolative decomposition U^_i = P_i [I; G_i] U^_i|_i^ of (2.11), then
+// the nested working sets (3.18).
+//
+// One CTA compresses one node at a time (persistent over the level's nodes).
+// The r x m matrix W = U^_i^T lives row-major in shared memory when it fits
+// and in a per-CTA global slot (L2-resident) otherwise.  Threads own columns
+// (= points): every dot product and norm is summed sequentially in the same
+// order as the CPU oracle, and the file is compiled with --fmad=false, so the
+// pivots, ranks and G of a node are bit-identical to the oracle's whenever
+// its inputs are.  All arithmetic is FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace smash {
+
+struct CompressArgs {
+    int d, p, r, level;
+    double tol, f, s;
+    double lo[3];
+    double anchors[kMaxP];
+    int64_t n0, nl;
+    const int32_t *leaf;
+    const uint64_t *cell;
+    const int64_t *start;
+    const int32_t *count;
+    const int32_t *child0;
+    const int32_t *nchild;
+    const double *pts;        // sorted coordinates, stride 4
+    const int64_t *skel_gidx; // skeleton slot -> sorted point index (children's working sets)
+    int32_t *m;
+    int32_t *k;
+    int64_t *in_off;
+    int64_t *sk_off;
+    const int64_t *loc_off;
+    const int64_t *g_off;
+    int32_t *loc;
+    int64_t *skg_tmp;
+    double *G;
+    int32_t *nswaps;
+    double *work;             // per-CTA slots of slot_doubles
+    int64_t slot_doubles;
+    int m_cap;
+    int w_in_smem;
+};
+
+// ---------------------------------------------------------------- setup
+// m and the input offset of each node of the level: leaves own their point
+// range (3.6); a parent's working set is its children's skeletons (3.18),
+// which are contiguous skeleton slots starting at the first child's.
+__global__ void level_setup_kernel(CompressArgs a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nl) return;
+    int64_t g = a.n0 + i;
+    if (a.leaf[g]) {
+        a.m[g] = a.count[g];
+        a.in_off[g] = a.start[g];
+    } else {
+        int c0 = a.child0[g], nc = a.nchild[g];
+        int s = 0;
+        for (int c = 0; c < nc; ++c) s += a.k[c0 + c];
+        a.m[g] = s;
+        a.in_off[g] = a.sk_off[c0];
+    }
+}
+
+// ---------------------------------------------------------------- helpers
+template <int NT>
+struct Smem {
+    double *nrm2;   // m_cap
+    double *v;      // r
+    double *rho;    // r
+    double *rval;   // NT/32
+    int64_t *ridx;  // NT/32
+    double *ctrl;   // 8
+    int *perm;      // m_cap
+    int *ex;        // m_cap
+    int *chunk;     // NT
+    double *W;      // r * m_cap when in shared memory
+};
+
+__device__ __forceinline__ bool better(double a, int64_t ia, double b, int64_t ib) {
+    return a > b || (a == b && ia < ib);
+}
+
+// block-wide maximum of (value, index), ties to the lowest index
+template <int NT>
+__device__ void block_argmax(double v, int64_t idx, Smem<NT> &sh, double &ov, int64_t &oi) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int64_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (better(v2, i2, v, idx)) { v = v2; idx = i2; }
+    }
+    if (lane == 0) { sh.rval[w] = v; sh.ridx[w] = idx; }
+    __syncthreads();
+    if (w == 0) {
+        v = lane < NT / 32 ? sh.rval[lane] : -1.0;
+        idx = lane < NT / 32 ? sh.ridx[lane] : INT64_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            int64_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (better(v2, i2, v, idx)) { v = v2; idx = i2; }
+        }
+        if (lane == 0) { sh.rval[0] = v; sh.ridx[0] = idx; }
+    }
+    __syncthreads();
+    ov = sh.rval[0];
+    oi = sh.ridx[0];
+    __syncthreads();
+}
+
+// ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n)
+__device__ __forceinline__ double lagrange(int p, const double *anch, int m, double t) {
+    double v = 1.0;
+    for (int n = 0; n < p; ++n) {
+        if (n == m) continue;
+        double num = t - anch[n];
+        double den = anch[m] - anch[n];
+        v = v * (num / den);
+    }
+    return v;
+}
+
+// column c of W = U^^T for the point at sorted index gid, in the cell of node g
+template <int PMAX>
+__device__ void basis_column(const CompressArgs &a, int64_t g, int64_t gid, double *W, int ld, int c) {
+    double h = ldexp(a.s, 1 - a.level);
+    double half = 0.5 * h;
+    double L[3][PMAX];
+    for (int ax = 0; ax < a.d; ++ax) {
+        double centre = a.lo[ax] + ((double)a.cell[g * 3 + ax] + 0.5) * h;
+        double t = (a.pts[gid * 4 + ax] - centre) / half;
+        for (int mm = 0; mm < a.p; ++mm) L[ax][mm] = lagrange(a.p, a.anchors, mm, t);
+    }
+    for (int kk = 0; kk < a.r; ++kk) {
+        int rem = kk, idx[3] = {0, 0, 0};
+        for (int ax = a.d - 1; ax >= 0; --ax) { idx[ax] = rem % a.p; rem /= a.p; }
+        double v = L[0][idx[0]];
+        for (int ax = 1; ax < a.d; ++ax) v = v * L[ax][idx[ax]];
+        W[(int64_t)kk * ld + c] = v;
+    }
+}
+
+__device__ __forceinline__ int64_t working_gid(const CompressArgs &a, int64_t g, int pos) {
+    return a.leaf[g] ? a.start[g] + pos : a.skel_gidx[a.in_off[g] + pos];
+}
+
+// Householder QR of W (r x m, row-major, leading dimension ld).  With pivot:
+// largest remaining column norm (ties: lowest position), stop before step j
+// when |R_jj| <= tol |R_00|; returns the number of steps.  Without pivot:
+// exactly ksteps steps in the current column order.
+template <int NT>
+__device__ int qr_steps(double *W, int ld, int r, int m, Smem<NT> &sh, bool pivot, int ksteps, double tol) {
+    const int tid = threadIdx.x;
+    int kmax = pivot ? min(r, m) : ksteps;
+    if (pivot) {
+        for (int c = tid; c < m; c += NT) {
+            double s2 = 0.0;
+            for (int i = 0; i < r; ++i) {
+                double x = W[(int64_t)i * ld + c];
+                s2 = s2 + x * x;
+            }
+            sh.nrm2[c] = s2;
+        }
+        __syncthreads();
+    }
+    double r00 = 0.0;
+    for (int j = 0; j < kmax; ++j) {
+        if (pivot) {
+            double best = -1.0;
+            int64_t bi = INT64_MAX;
+            for (int c = j + tid; c < m; c += NT)
+                if (better(sh.nrm2[c], c, best, bi)) { best = sh.nrm2[c]; bi = c; }
+            double val;
+            int64_t piv;
+            block_argmax<NT>(best, bi, sh, val, piv);
+            double nrm = sqrt(val);
+            if (j == 0) {
+                r00 = nrm;
+                if (nrm == 0.0) return 0;
+            } else if (nrm <= tol * r00) {
+                return j;
+            }
+            if (piv != j) {
+                for (int i = tid; i < r; i += NT) {
+                    double t = W[(int64_t)i * ld + j];
+                    W[(int64_t)i * ld + j] = W[(int64_t)i * ld + piv];
+                    W[(int64_t)i * ld + piv] = t;
+                }
+                if (tid == 0) {
+                    int tp = sh.perm[j];
+                    sh.perm[j] = sh.perm[piv];
+                    sh.perm[piv] = tp;
+                }
+                __syncthreads();
+            }
+        }
+        if (tid == 0) {
+            double alpha = W[(int64_t)j * ld + j];
+            double sigma = 0.0;
+            for (int i = j + 1; i < r; ++i) {
+                double x = W[(int64_t)i * ld + j];
+                sigma = sigma + x * x;
+            }
+            if (sigma == 0.0) {
+                sh.ctrl[0] = 1.0;  // skip: the column is already reduced
+            } else {
+                double nrm = sqrt(alpha * alpha + sigma);
+                double beta = alpha <= 0.0 ? nrm : -nrm;
+                sh.ctrl[0] = 0.0;
+                sh.ctrl[1] = (beta - alpha) / beta;  // tau
+                sh.ctrl[2] = alpha - beta;           // divisor of v
+                sh.ctrl[3] = beta;
+            }
+        }
+        __syncthreads();
+        const bool skip = sh.ctrl[0] != 0.0;
+        const double tau = sh.ctrl[1], den = sh.ctrl[2], beta = sh.ctrl[3];
+        if (!skip) {
+            for (int i = j + 1 + tid; i < r; i += NT) sh.v[i] = W[(int64_t)i * ld + j] / den;
+            __syncthreads();
+        }
+        for (int c = j + 1 + tid; c < m; c += NT) {
+            double s2 = 0.0;
+            if (!skip) {
+                double w = W[(int64_t)j * ld + c];
+                for (int i = j + 1; i < r; ++i) w = w + sh.v[i] * W[(int64_t)i * ld + c];
+                double tw = tau * w;
+                W[(int64_t)j * ld + c] = W[(int64_t)j * ld + c] - tw;
+                for (int i = j + 1; i < r; ++i) {
+                    double x = W[(int64_t)i * ld + c] - tw * sh.v[i];
+                    W[(int64_t)i * ld + c] = x;
+                    s2 = s2 + x * x;
+                }
+            } else {
+                for (int i = j + 1; i < r; ++i) {
+                    double x = W[(int64_t)i * ld + c];
+                    s2 = s2 + x * x;
+                }
+            }
+            if (pivot) sh.nrm2[c] = s2;
+        }
+        __syncthreads();
+        if (!skip) {
+            if (tid == 0) W[(int64_t)j * ld + j] = beta;
+            for (int i = j + 1 + tid; i < r; i += NT) W[(int64_t)i * ld + j] = 0.0;
+        }
+        __syncthreads();
+    }
+    return kmax;
+}
+
+// exclusive prefix of flag[0..m) into ex[0..m)
+template <int NT>
+__device__ void block_scan_flags(Smem<NT> &sh, int m) {
+    const int tid = threadIdx.x;
+    int per = (m + NT - 1) / NT;
+    int b0 = tid * per, b1 = min(m, b0 + per);
+    int cnt = 0;
+    for (int i = b0; i < b1; ++i) cnt += sh.ex[i];
+    sh.chunk[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int t = 0; t < NT; ++t) { int c = sh.chunk[t]; sh.chunk[t] = run; run += c; }
+    }
+    __syncthreads();
+    int run = sh.chunk[tid];
+    for (int i = b0; i < b1; ++i) { int f = sh.ex[i]; sh.ex[i] = run; run += f; }
+    __syncthreads();
+}
+
+template <int NT, int PMAX>
+__global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem<NT> sh;
+    {
+        double *dp = reinterpret_cast<double *>(smraw);
+        sh.nrm2 = dp; dp += a.m_cap;
+        sh.v = dp; dp += a.r;
+        sh.rho = dp; dp += a.r;
+        sh.rval = dp; dp += NT / 32;
+        sh.ctrl = dp; dp += 8;
+        sh.ridx = reinterpret_cast<int64_t *>(dp); dp += NT / 32;
+        sh.W = a.w_in_smem ? dp : nullptr;
+        if (a.w_in_smem) dp += (int64_t)a.r * a.m_cap;
+        int *ip = reinterpret_cast<int *>(dp);
+        sh.perm = ip; ip += a.m_cap;
+        sh.ex = ip; ip += a.m_cap;
+        sh.chunk = ip;
+    }
+    const int tid = threadIdx.x;
+    double *slot = a.work + (int64_t)blockIdx.x * a.slot_doubles;
+    double *W = a.w_in_smem ? sh.W : slot;
+    double *X = slot + (a.w_in_smem ? 0 : (int64_t)a.r * a.m_cap);  // R11^{-1}, k x k
+    const int r = a.r;
+
+    for (int64_t ni = blockIdx.x; ni < a.nl; ni += gridDim.x) {
+        const int64_t g = a.n0 + ni;
+        const int m = a.m[g];
+        if (m == 0) {
+            if (tid == 0) { a.k[g] = 0; a.nswaps[g] = 0; }
+            continue;
+        }
+        const int ld = m;
+        // 1. W = U^^T
+        for (int c = tid; c < m; c += NT) {
+            basis_column<PMAX>(a, g, working_gid(a, g, c), W, ld, c);
+            sh.perm[c] = c;
+        }
+        __syncthreads();
+        // 2. column-pivoted QR with the rank cut
+        int k = qr_steps<NT>(W, ld, r, m, sh, true, 0, a.tol);
+        // 3. Gu-Eisenstat swaps until max (A_ij^2 + gamma_j^2 / omega_i^2) <= f^2
+        int nsw = 0;
+        for (;;) {
+            if (k == 0 || k == m) break;
+            const int mk = m - k;
+            for (int u = tid; u < mk; u += NT)
+                for (int t = k - 1; t >= 0; --t) {
+                    double s = W[(int64_t)t * ld + k + u];
+                    for (int q = t + 1; q < k; ++q) s = s - W[(int64_t)t * ld + q] * W[(int64_t)q * ld + k + u];
+                    W[(int64_t)t * ld + k + u] = s / W[(int64_t)t * ld + t];
+                }
+            for (int c = tid; c < k; c += NT)
+                for (int t = k - 1; t >= 0; --t) {
+                    double s = (t == c) ? 1.0 : 0.0;
+                    for (int q = t + 1; q < k; ++q) s = s - W[(int64_t)t * ld + q] * X[(int64_t)q * k + c];
+                    X[(int64_t)t * k + c] = s / W[(int64_t)t * ld + t];
+                }
+            __syncthreads();
+            for (int t = tid; t < k; t += NT) {
+                double s = 0.0;
+                for (int c = 0; c < k; ++c) {
+                    double x = X[(int64_t)t * k + c];
+                    s = s + x * x;
+                }
+                sh.rho[t] = s;
+            }
+            for (int u = tid; u < mk; u += NT) {
+                double s = 0.0;
+                for (int i = k; i < r; ++i) {
+                    double x = W[(int64_t)i * ld + k + u];
+                    s = s + x * x;
+                }
+                sh.nrm2[u] = s;  // gamma_u^2
+            }
+            __syncthreads();
+            double best = -1.0;
+            int64_t bi = INT64_MAX;
+            const int64_t tot = (int64_t)k * mk;
+            for (int64_t e = tid; e < tot; e += NT) {
+                int t = (int)(e / mk), u = (int)(e % mk);
+                double av = W[(int64_t)t * ld + k + u];
+                double val = av * av + sh.nrm2[u] * sh.rho[t];
+                if (better(val, e, best, bi)) { best = val; bi = e; }
+            }
+            double bv;
+            int64_t be;
+            block_argmax<NT>(best, bi, sh, bv, be);
+            if (bv <= a.f * a.f) break;
+            if (nsw >= kMaxSwaps) { nsw = -1; break; }
+            if (tid == 0) {
+                int bt = (int)(be / mk), bu = (int)(be % mk);
+                int tp = sh.perm[bt];
+                sh.perm[bt] = sh.perm[k + bu];
+                sh.perm[k + bu] = tp;
+            }
+            ++nsw;
+            __syncthreads();
+            for (int c = tid; c < m; c += NT) basis_column<PMAX>(a, g, working_gid(a, g, sh.perm[c]), W, ld, c);
+            __syncthreads();
+            qr_steps<NT>(W, ld, r, m, sh, false, k, a.tol);
+        }
+        // 4. canonical form: skeleton and rest in ascending working-set order
+        const int mk = m - k;
+        for (int pos = tid; pos < m; pos += NT) sh.ex[pos] = 0;
+        __syncthreads();
+        for (int t = tid; t < k; t += NT) sh.ex[sh.perm[t]] = 1;
+        __syncthreads();
+        block_scan_flags<NT>(sh, m);
+        const int64_t lo = a.loc_off[g];
+        for (int t = tid; t < k; t += NT) {
+            int pos = sh.perm[t];
+            int tp = sh.ex[pos];
+            a.loc[lo + tp] = pos;
+            a.skg_tmp[lo + tp] = working_gid(a, g, pos);
+        }
+        for (int u = tid; u < mk; u += NT) {
+            int pos = sh.perm[k + u];
+            a.loc[lo + k + (pos - sh.ex[pos])] = pos;
+        }
+        const int64_t go = a.g_off[g];
+        for (int64_t e = tid; e < (int64_t)k * mk; e += NT) {
+            int t = (int)(e / mk), u = (int)(e % mk);
+            int tp = sh.ex[sh.perm[t]];
+            int pu = sh.perm[k + u];
+            int up = pu - sh.ex[pu];
+            a.G[go + (int64_t)up * k + tp] = W[(int64_t)t * ld + k + u];
+        }
+        if (tid == 0) { a.k[g] = k; a.nswaps[g] = nsw; }
+        __syncthreads();
+    }
+}
+
+// skeleton slots of the level, compacted in node order
+__global__ void compact_skeleton_kernel(int64_t n0, int64_t nl, const int32_t *__restrict__ k,
+                                        const int64_t *__restrict__ sk_off, const int64_t *__restrict__ loc_off,
+                                        const int64_t *__restrict__ skg_tmp, const double *__restrict__ pts,
+                                        int64_t *__restrict__ skel_gidx, double *__restrict__ skel_xyz) {
+    int64_t g = n0 + blockIdx.x;
+    int kk = k[g];
+    for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+        int64_t gid = skg_tmp[loc_off[g] + t];
+        int64_t slot = sk_off[g] + t;
+        skel_gidx[slot] = gid;
+        reinterpret_cast<P4 *>(skel_xyz)[slot] = reinterpret_cast<const P4 *>(pts)[gid];
+    }
+}
+
+// upper bounds: k <= min(r, count), m <= leaf ? count : sum_children min(r, count_c),
+// |G| <= max_{k <= min(r,m)} (m - k) k
+__global__ void bounds_kernel(int64_t nn, int r, const int32_t *__restrict__ leaf, const int32_t *__restrict__ cnt,
+                              const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
+                              int64_t *__restrict__ kub, int64_t *__restrict__ mub, int64_t *__restrict__ gub) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nn) return;
+    int64_t m;
+    if (g == 0) {
+        m = 0;  // the root is never compressed
+    } else if (leaf[g]) {
+        m = cnt[g];
+    } else {
+        m = 0;
+        for (int c = 0; c < nchild[g]; ++c) m += min((int64_t)r, (int64_t)cnt[child0[g] + c]);
+    }
+    int64_t kmax = min((int64_t)r, m);
+    int64_t kh = m / 2;
+    int64_t kb = kh <= kmax ? kh : kmax;
+    int64_t gb = (m - kb) * kb;
+    if (kh + 1 <= kmax) gb = max(gb, (m - kh - 1) * (kh + 1));
+    kub[g] = g == 0 ? 0 : min((int64_t)r, (int64_t)cnt[g]);
+    mub[g] = m;
+    gub[g] = gb;
+}
+
+static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
+    cudaStream_t st = h->stream;
+    const int64_t nn = h->nnodes;
+    const int32_t *cnt = rows ? h->rc : h->cc;
+    const int64_t *start = rows ? h->rs : h->cs;
+    const double *pts = rows ? h->xs : h->ys;
+    S.m = h->mem.alloc<int32_t>(nn);
+    S.k = h->mem.alloc<int32_t>(nn);
+    S.in_off = h->mem.alloc<int64_t>(nn);
+    S.sk_off = h->mem.alloc<int64_t>(nn);
+    S.loc_off = h->mem.alloc<int64_t>(nn + 1);
+    S.g_off = h->mem.alloc<int64_t>(nn + 1);
+    S.nswaps = h->mem.alloc<int32_t>(nn);
+    CK(cudaMemsetAsync(S.m, 0, nn * 4, st));
+    CK(cudaMemsetAsync(S.k, 0, nn * 4, st));
+    CK(cudaMemsetAsync(S.nswaps, 0, nn * 4, st));
+    CK(cudaMemsetAsync(S.sk_off, 0, nn * 8, st));
+    CK(cudaMemsetAsync(S.in_off, 0, nn * 8, st));
+    int64_t *kub = scratch.alloc<int64_t>(nn), *mub = scratch.alloc<int64_t>(nn), *gub = scratch.alloc<int64_t>(nn);
+    int64_t *tot = scratch.alloc<int64_t>(4);
+    bounds_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, h->r, h->leaf, cnt, h->child0, h->nchild, kub,
+                                                                 mub, gub);
+    LAUNCHED();
+    int64_t *kub_off = scratch.alloc<int64_t>(nn);
+    exclusive_scan<int64_t>(kub, kub_off, nn, nullptr, tot + 0, st, scratch);
+    exclusive_scan<int64_t>(mub, S.loc_off, nn, nullptr, tot + 1, st, scratch);
+    exclusive_scan<int64_t>(gub, S.g_off, nn, nullptr, tot + 2, st, scratch);
+    // per-level maximum of the m bound
+    std::vector<int64_t> lmax(h->L + 1, 0);
+    int64_t *lm = scratch.alloc<int64_t>(h->L + 1);
+    for (int l = 2; l <= h->L; ++l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        reduce_max(mub + n0, nl, lm + l, st);
+    }
+    int64_t ht[3];
+    CK(cudaMemcpyAsync(ht, tot, 3 * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lmax.data(), lm, (h->L + 1) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    S.skel_cap = std::max<int64_t>(ht[0], 1);
+    S.total_loc = ht[1];
+    S.total_g = ht[2];
+    S.mub_max = lmax;
+    S.loc = h->mem.alloc<int32_t>(std::max<int64_t>(S.total_loc, 1));
+    S.skg_tmp = scratch.alloc<int64_t>(std::max<int64_t>(S.total_loc, 1));
+    S.G = h->mem.alloc<double>(std::max<int64_t>(S.total_g, 1));
+    S.skel_gidx = h->mem.alloc<int64_t>(S.skel_cap);
+    S.skel_xyz = h->mem.alloc<double>(S.skel_cap * 4);
+    int64_t *base = tot + 3;
+    CK(cudaMemsetAsync(base, 0, 8, st));
+
+    // one persistent launch per level, deepest first
+    constexpr int NT = 128;
+    double *work = nullptr;
+    int64_t work_cap = 0;
+    for (int l = h->L; l >= 2; --l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        int m_cap = (int)std::max<int64_t>(lmax[l], 1);
+        CompressArgs a;
+        a.d = h->dim; a.p = h->order; a.r = h->r; a.level = l;
+        a.tol = h->tol; a.f = h->f; a.s = h->s;
+        for (int i = 0; i < 3; ++i) a.lo[i] = h->lo[i];
+        for (int i = 0; i < kMaxP; ++i) a.anchors[i] = i < h->order ? h->anchors[i] : 0.0;
+        a.n0 = n0; a.nl = nl;
+        a.leaf = h->leaf; a.cell = h->cell; a.start = start; a.count = cnt;
+        a.child0 = h->child0; a.nchild = h->nchild; a.pts = pts; a.skel_gidx = S.skel_gidx;
+        a.m = S.m; a.k = S.k; a.in_off = S.in_off; a.sk_off = S.sk_off; a.loc_off = S.loc_off;
+        a.g_off = S.g_off; a.loc = S.loc; a.skg_tmp = S.skg_tmp; a.G = S.G; a.nswaps = S.nswaps;
+        a.m_cap = m_cap;
+        level_setup_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(a);
+        LAUNCHED();
+        size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
+                           sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
+        size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
+        a.w_in_smem = (base_smem + w_bytes) <= 160 * 1024;
+        size_t smem = base_smem + (a.w_in_smem ? w_bytes : 0);
+        a.slot_doubles = (a.w_in_smem ? 0 : (int64_t)h->r * m_cap) + (int64_t)h->r * h->r;
+        auto kern = h->order <= 16 ? compress_kernel<NT, 16> : compress_kernel<NT, kMaxP>;
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+        if (per_sm < 1) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", smem);
+        int64_t grid = std::min<int64_t>(nl, (int64_t)per_sm * h->num_sms);
+        int64_t need = grid * a.slot_doubles;
+        if (need > work_cap) {
+            if (work) scratch.free(work);
+            work = scratch.alloc<double>(need);
+            work_cap = need;
+        }
+        a.work = work;
+        kern<<<(unsigned)grid, NT, smem, st>>>(a);
+        LAUNCHED();
+        exclusive_scan<int32_t>(S.k + n0, S.sk_off + n0, nl, base, base, st, scratch);
+        compact_skeleton_kernel<<<(unsigned)nl, 128, 0, st>>>(n0, nl, S.k, S.sk_off, S.loc_off, S.skg_tmp, pts,
+                                                               S.skel_gidx, S.skel_xyz);
+        LAUNCHED();
+    }
+    int64_t total_skel = 0;
+    CK(cudaMemcpyAsync(&total_skel, base, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    S.total_skel = total_skel;
+    if (work) scratch.free(work);
+    scratch.free(kub); scratch.free(mub); scratch.free(gub); scratch.free(kub_off);
+    scratch.free(lm); scratch.free(tot); scratch.free(S.skg_tmp);
+    S.skg_tmp = nullptr;
+}
+
+void build_compression(smash_h2 *h, Arena &scratch) {
+    compress_side(h, h->row, true, scratch);
+    if (h->same) {
+        h->col = &h->row;
+    } else {
+        compress_side(h, h->colside, false, scratch);
+        h->col = &h->colside;
+    }
+}
+
+}  // namespace smash

@@ -1,0 +1,169 @@
+// internal.cuh -- shared declarations of the CUDA library behind include/smash.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/smash.h"
+
+namespace smash {
+
+// one point (or a padded 4-vector), 32-byte aligned for vector loads
+struct __align__(32) P4 {
+    double x, y, z, w;
+};
+
+constexpr int kMaxR = 512;     // largest order^dim
+constexpr int kMaxP = 64;      // largest order
+constexpr int kMaxNrhs = 64;
+constexpr int kMaxSwaps = 1000;  // cap of the Gu-Eisenstat swap loop per node
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    smash_status status;
+    std::string msg;
+};
+[[noreturn]] void fail(smash_status st, const char *fmt, ...);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+#define CK(x) ::smash::check_cuda((x), #x, __FILE__, __LINE__)
+
+extern std::atomic<uint64_t> g_launches;
+#define LAUNCHED() \
+    do { ::smash::g_launches.fetch_add(1, std::memory_order_relaxed); CK(cudaGetLastError()); } while (0)
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered device allocations owned by one object; freed on release().
+class Arena {
+  public:
+    explicit Arena(cudaStream_t s = nullptr) : stream_(s) {}
+    ~Arena() { release(); }
+    Arena(const Arena &) = delete;
+    Arena &operator=(const Arena &) = delete;
+    void set_stream(cudaStream_t s) { stream_ = s; }
+    template <class T>
+    T *alloc(size_t n) {
+        return static_cast<T *>(raw(n * sizeof(T)));
+    }
+    void *raw(size_t bytes);
+    void free(void *p);
+    void release();
+    size_t bytes() const { return bytes_; }
+
+  private:
+    struct Blk { void *p; size_t n; };
+    cudaStream_t stream_;
+    std::vector<Blk> blocks_;
+    size_t bytes_ = 0;
+};
+
+// ---------------------------------------------------------------- primitives
+// Exclusive scan of n values; out[i] = base + sum_{j<i} in[j] (base read from
+// device memory when base_dev != nullptr); *total_dev = base + sum, if given.
+template <class T>
+void exclusive_scan(const T *in, int64_t *out, int64_t n, const int64_t *base_dev, int64_t *total_dev,
+                    cudaStream_t s, Arena &scratch);
+
+// Stable LSD radix sort of 64-bit keys on their low `bits` bits, carrying
+// optional int32 values.  Sorts in place (keys, vals) using scratch buffers.
+void radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int bits, cudaStream_t s, Arena &scratch);
+
+// Device maximum of an int64 array into *out_dev (n >= 1).
+void reduce_max(const int64_t *in, int64_t n, int64_t *out_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- representation
+struct Side {
+    // per node
+    int32_t *m = nullptr;      // |i_bar|
+    int32_t *k = nullptr;      // |i_hat|
+    int64_t *in_off = nullptr; // leaf: first point (sorted); parent: skeleton slot of child0
+    int64_t *sk_off = nullptr; // first skeleton slot of the node
+    int64_t *loc_off = nullptr;// offset into loc (upper-bound prefix of m)
+    int64_t *g_off = nullptr;  // offset into G (upper-bound prefix of max (m-k)k)
+    int32_t *nswaps = nullptr;
+    // flat
+    int32_t *loc = nullptr;    // per node: k skeleton positions in i_bar, then m-k rest positions
+    int64_t *skg_tmp = nullptr;// per node at loc_off: skeleton point indices before compaction
+    double *G = nullptr;
+    int64_t *skel_gidx = nullptr; // per skeleton slot: sorted point index
+    double *skel_xyz = nullptr;   // per skeleton slot: coordinates, stride 4
+    int64_t total_skel = 0, total_loc = 0, total_g = 0, skel_cap = 0;
+    std::vector<int64_t> mub_max;  // per level, upper bound of m
+};
+
+struct Profile {
+    bool on = false;
+    double ms[10] = {0};
+};
+
+}  // namespace smash
+
+struct smash_h2 {
+    int dim = 0, kernel_id = 0, leaf_size = 0, order = 0, r = 0, same = 1, bits = 0;
+    double tau = 0.7, f = 2.0, tol = 1e-8;
+    int64_t nx = 0, ny = 0;
+    double lo[3] = {0, 0, 0}, s = 1.0;
+    double anchors[smash::kMaxP];
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+    smash::Arena mem;
+    // sorted points
+    int64_t *permx = nullptr, *permy = nullptr;
+    uint64_t *keyx = nullptr, *keyy = nullptr;
+    double *xs = nullptr, *ys = nullptr;  // stride 4
+    // tree
+    int L = 0;
+    std::vector<int64_t> lvl_off;  // host copy, L + 1 entries
+    int64_t nnodes = 0, nleaves = 0;
+    int32_t *level = nullptr, *leaf = nullptr, *parent = nullptr, *child0 = nullptr, *nchild = nullptr;
+    int64_t *rs = nullptr, *cs = nullptr;
+    int32_t *rc = nullptr, *cc = nullptr;
+    uint64_t *cell = nullptr;  // nnodes x 3
+    int32_t *leaf_list = nullptr;
+    int32_t *nonroot_list = nullptr;
+    // lists
+    int64_t nadm = 0, nnear = 0;
+    int64_t *adm_ptr = nullptr, *near_ptr = nullptr;
+    int32_t *adm_col = nullptr, *near_col = nullptr;
+    // compression
+    smash::Side row, colside;
+    smash::Side *col = nullptr;  // == &row when same
+    // statistics
+    int64_t swaps = 0, swap_cap_hits = 0, coupling_pairs = 0, near_pairs = 0;
+    int64_t rest_row = 0, g_row = 0, rest_col = 0, g_col = 0;  // exact sums of m-k and (m-k)k
+    smash::Profile prof_build, prof_mv;
+};
+
+namespace smash {
+
+// phases of the build (each in its own translation unit)
+void build_geometry(smash_h2 *h, const double *x_dev, const double *y_dev, Arena &scratch);
+void build_tree(smash_h2 *h, Arena &scratch);
+void build_lists(smash_h2 *h, Arena &scratch);
+void build_compression(smash_h2 *h, Arena &scratch);
+void build_stats(smash_h2 *h, Arena &scratch);
+
+// matvec in FP64: X_dev (ny x nrhs), Y_dev (nx x nrhs), both device
+void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
+                Profile *prof);
+
+bool profiling_enabled();
+
+// Helper for event-timed phases.
+struct PhaseTimer {
+    cudaStream_t s;
+    Profile *p;
+    cudaEvent_t ev[11];
+    int n = 0;
+    PhaseTimer(cudaStream_t s_, Profile *p_) : s(s_), p(p_) {}
+    void mark();
+    void finish(int first_slot);
+    ~PhaseTimer();
+};
+
+}  // namespace smash

@@ -560,3 +560,17 @@ def test_h2_rectangular_cauchy_close_to_dense():
     h = oracle.H2(x, 3, 32, 16, 1e-10, y=y)
     ref = kernel_matrix(3, x, y) @ q
     assert rel(h.matvec(q), ref) < 1e-6
+
+
+def test_h2_matvec_on_selected_leaves_equals_full_matvec():
+    x = si.uniform_cube(5000, 3, 77)
+    q = si.rhs(5000, 3, 78)
+    h = oracle.H2(x, 1, 64, 3, 1e-8)
+    e = h.export()
+    leaves = np.flatnonzero(e["leaf"])[[0, 5, -1]].astype(np.int32)
+    zsel = h.matvec_leaves(q, leaves)
+    zall = h.matvec(q)
+    rows = np.concatenate([e["permx"][e["rs"][g]:e["rs"][g] + e["rc"][g]] for g in leaves])
+    assert np.array_equal(zsel[rows], zall[rows])
+    others = np.setdiff1d(np.arange(5000), rows)
+    assert np.all(np.isnan(zsel[others]))
