@@ -125,6 +125,32 @@ SMASH_API smash_status smash_matvec(smash_handle h, const double *X, double *Y, 
 SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision,
                              void *stream);
 
+/*
+ * smash_matvec_noalloc -- the FP64 matvec of smash_matvec_ex that allocates
+ * no device memory, for callers that cannot allocate while they run (a host
+ * that gives all free device memory to its own pool allocator up front, or a
+ * real-time loop that forbids allocation after start-up).  The paper has no
+ * counterpart: this is a deployment variant of the same computation.
+ *   X  ny x nrhs float64 DEVICE memory, caller's point order
+ *   Y  nx x nrhs float64 DEVICE memory, overwritten
+ *   stream  cudaStream_t, NULL = the handle's stream; asynchronous
+ * Its scratch (the q, z, q^ and z^ vectors) lives in one static device array
+ * of SMASH_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library
+ * holds until the process exits; problems whose scratch does not fit, i.e.
+ * 8 * ldq * (nx + ny + skeleton slots of rows and columns) bytes beyond that
+ * maximum (ldq = nrhs rounded up to a power of two, or to a multiple of 32
+ * above 32), are rejected with SMASH_EINVAL and a message.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  The
+ * handle's device must be the current device.  Every call overwrites each
+ * scratch region before reading it, so no state carries over between calls,
+ * but all calls share the one array: calls whose GPU work overlaps (on
+ * different streams, or from different threads) race and must be ordered by
+ * the caller.  Errors: SMASH_EINVAL, SMASH_ECUDA.
+ */
+#define SMASH_NOALLOC_SCRATCH_BYTES (64u << 20)
+SMASH_API smash_status smash_matvec_noalloc(smash_handle h, const double *X, double *Y, int nrhs, void *stream);
+
 /* Releases the handle and its device memory; NULL-safe; waits for the
  * handle's pending work first. */
 SMASH_API void smash_free(smash_handle h);

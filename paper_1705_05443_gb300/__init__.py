@@ -20,7 +20,8 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "SmashError", "smash_build", "smash_build_xy", "smash_matvec", "smash_matvec_ex", "smash_free",
+    "SmashError", "smash_build", "smash_build_xy", "smash_matvec", "smash_matvec_ex",
+    "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
     "smash_last_profile", "H2Matrix", "load_library", "library_path",
@@ -96,6 +97,8 @@ def load_library(build: bool = True):
     lib.smash_matvec.restype = i32
     lib.smash_matvec_ex.argtypes = [P, P, P, i32, i32, P]
     lib.smash_matvec_ex.restype = i32
+    lib.smash_matvec_noalloc.argtypes = [P, P, P, i32, P]
+    lib.smash_matvec_noalloc.restype = i32
     lib.smash_free.argtypes = [P]
     lib.smash_free.restype = None
     lib.smash_info.argtypes = [P, P]
@@ -188,6 +191,14 @@ def smash_matvec_ex(h, X, Y, precision: int = SMASH_PREC_F64, stream=None, nrhs:
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
     _check(lib.smash_matvec_ex(h, _ptr(X), _ptr(Y), nrhs, precision, _stream_ptr(stream)))
+    return Y
+
+
+def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
+    """Y = A^ X without device allocation (X, Y device tensors); see smash.h."""
+    lib = load_library()
+    nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check(lib.smash_matvec_noalloc(h, _ptr(X), _ptr(Y), nrhs, _stream_ptr(stream)))
     return Y
 
 

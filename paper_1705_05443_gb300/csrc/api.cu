@@ -19,6 +19,8 @@ static smash_status record(const Error &e) {
     return e.status;
 }
 
+void set_last_error(const char *msg) { t_last_error = msg ? msg : ""; }
+
 static bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);

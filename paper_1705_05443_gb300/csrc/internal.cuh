@@ -152,7 +152,16 @@ void build_stats(smash_h2 *h, Arena &scratch);
 void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
                 Profile *prof);
 
+// The same matvec with caller-provided device scratch (no allocation):
+// matvec_f64_scratch_bytes is the scratch it needs for nrhs right-hand sides.
+size_t matvec_f64_scratch_bytes(const smash_h2 *h, int nrhs);
+void matvec_f64_scratch(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
+                        void *scratch, size_t scratch_bytes);
+
 bool profiling_enabled();
+
+// Message returned by smash_last_error() on this host thread.
+void set_last_error(const char *msg);
 
 // Helper for event-timed phases.
 struct PhaseTimer {

@@ -307,4 +307,76 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
     tmp.release();
 }
 
+// ------------------------------------------------------------------ caller scratch
+// The passes of matvec_f64 with qs, zs, q^ and z^ carved out of a caller
+// buffer instead of stream-ordered allocations.  Every carved region is
+// written in full before it is read (gather writes qs, the near field writes
+// zs for every point, the upward pass writes every column skeleton slot, the
+// coupling writes every row skeleton slot), so nothing needs clearing.
+static size_t carve(size_t &off, size_t bytes) {
+    size_t at = (off + 255) & ~size_t(255);
+    off = at + bytes;
+    return at;
+}
+
+size_t matvec_f64_scratch_bytes(const smash_h2 *h, int nrhs) {
+    int ldq, RC;
+    rhs_layout(nrhs, ldq, RC);
+    size_t off = 0;
+    carve(off, sizeof(double) * (size_t)h->ny * ldq);
+    carve(off, sizeof(double) * (size_t)h->nx * ldq);
+    carve(off, sizeof(double) * (size_t)std::max<int64_t>(h->col->total_skel, 1) * ldq);
+    carve(off, sizeof(double) * (size_t)std::max<int64_t>(h->row.total_skel, 1) * ldq);
+    return off;
+}
+
+void matvec_f64_scratch(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, void *scratch,
+                        size_t scratch_bytes) {
+    const Side &R = h->row;
+    const Side &Cs = *h->col;
+    int ldq, RC;
+    rhs_layout(nrhs, ldq, RC);
+    if (matvec_f64_scratch_bytes(h, nrhs) > scratch_bytes) fail(SMASH_EINVAL, "scratch too small");
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    size_t off = 0;
+    double *qs = reinterpret_cast<double *>(base + carve(off, sizeof(double) * (size_t)h->ny * ldq));
+    double *zs = reinterpret_cast<double *>(base + carve(off, sizeof(double) * (size_t)h->nx * ldq));
+    double *qhat = reinterpret_cast<double *>(
+        base + carve(off, sizeof(double) * (size_t)std::max<int64_t>(Cs.total_skel, 1) * ldq));
+    double *zhat = reinterpret_cast<double *>(
+        base + carve(off, sizeof(double) * (size_t)std::max<int64_t>(R.total_skel, 1) * ldq));
+    gather_rhs_kernel<<<(unsigned)((h->ny * ldq + 255) / 256), 256, 0, s>>>(X, nrhs, h->permy, h->ny, ldq, qs);
+    LAUNCHED();
+    {
+        KsumArgs a{};
+        a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
+        a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
+        a.xt = h->xs; a.ys = h->ys; a.qv = qs; a.out = zs; a.ldq = ldq;
+        ksum(h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+    }
+    for (int l = h->L; l >= 2; --l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassArgs p{n0, h->leaf, Cs.m, Cs.k, Cs.in_off, Cs.sk_off, Cs.loc_off, Cs.g_off, Cs.loc, Cs.G,
+                   qs, qhat, qhat, nullptr, ldq};
+        upward_kernel<<<(unsigned)nl, 256, 0, s>>>(p);
+        LAUNCHED();
+    }
+    if (h->nnodes > 1) {
+        KsumArgs a{};
+        a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
+        a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
+        a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
+        ksum(h->kernel_id, a, h->nnodes - 1, h->r, RC, s);
+    }
+    for (int l = 2; l <= h->L; ++l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassArgs p{n0, h->leaf, R.m, R.k, R.in_off, R.sk_off, R.loc_off, R.g_off, R.loc, R.G,
+                   nullptr, zhat, zhat, zs, ldq};
+        downward_kernel<<<(unsigned)nl, 256, 0, s>>>(p);
+        LAUNCHED();
+    }
+    scatter_rhs_kernel<<<(unsigned)((h->nx * nrhs + 255) / 256), 256, 0, s>>>(zs, ldq, h->permx, h->nx, nrhs, Y);
+    LAUNCHED();
+}
+
 }  // namespace smash
