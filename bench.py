@@ -165,7 +165,11 @@ def bench_ours(args, w):
     q = torch.from_numpy(q_np).to(dev)
     z = torch.empty_like(q)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library runs build and matvec on it and the
+    # timing events are recorded on it (the default stream's handle is NULL,
+    # which the C ABI reads as "the handle's own stream")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
 
     def step(host=False):
         if host:
@@ -191,6 +195,7 @@ def bench_ours(args, w):
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
+        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -251,7 +256,8 @@ def bench_ours(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "3d_invr uniform cube N=2^20", "n": n, "dim": 3, "kernel": "1/|x-y|",
+        "config": {"workload": "3d_invr uniform cube N=2^20" if n == 1 << 20 else f"3d_invr uniform cube N={n}",
+                   "n": n, "dim": 3, "kernel": "1/|x-y|",
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
                    "precision": "fp64", "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{ws}"},
@@ -288,8 +294,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_invr_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="point count (same recipe); for profiling cases")
     args = ap.parse_args()
     w = dict(si.WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
     if args.impl == "reference":
         bench_reference(args, w)
     else:
