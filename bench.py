@@ -35,8 +35,11 @@ UNIT = "points/s"
 CPU_SAMPLE_N = 32768      # oracle sample for cpu_baseline (same recipe, ~10-30 s of CPU work)
 REF_SAMPLE_N = 16384      # oracle sample per step of the reference arm
 FP64_FLOPS_PER_CLK_SM = 4  # 1.25 TFLOP/s nominal FP64 / (152 SMs x 2.07 GHz) ~= 4 (2 DFMA per clock)
+FP32_OPS_PER_CLK_SM = 128  # FP32 pipe lanes per SM: one arithmetic instruction per lane per clock
 NUM_SMS = 152
-PAIR_EVAL_FLOPS = 9        # squared distance (8) + reciprocal square root (1) per kernel entry
+PAIR_EVAL_FLOPS = 9        # FP64: squared distance (8) + reciprocal square root (1) per kernel entry
+DD_EVAL_OPS = 54           # double-float: FP32 instructions of one 1/|x-y| entry (difference, square, rsqrt + Newton)
+DD_MAC_OPS = 12            # double-float: FP32 instructions of one error-free multiply-accumulate
 
 
 def _dist():
@@ -171,13 +174,15 @@ def bench_ours(args, w):
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
 
-    def step(host=False):
+    prec = sm.SMASH_PREC_F32X2 if args.precision == "f32x2" else sm.SMASH_PREC_F64
+
+    def step(host=False, precision=prec):
         if host:
             h = sm.smash_build_xy(xh, None, w["kernel"], w["leaf"], w["order"], w["tol"], stream=stream)
-            sm.smash_matvec_ex(h, qh, zh, sm.SMASH_PREC_F64, stream=stream)
+            sm.smash_matvec_ex(h, qh, zh, precision, stream=stream)
         else:
             h = sm.smash_build_xy(x, None, w["kernel"], w["leaf"], w["order"], w["tol"], stream=stream)
-            sm.smash_matvec_ex(h, q, z, sm.SMASH_PREC_F64, stream=stream)
+            sm.smash_matvec_ex(h, q, z, precision, stream=stream)
         return h
 
     sm.smash_set_profiling(True)
@@ -238,6 +243,25 @@ def bench_ours(args, w):
         e2e_t.append(time.perf_counter() - t0)
         sm.smash_free(h)
     e2e_val = ws * n / statistics.median(e2e_t)
+
+    # context: the same step with the FP64 matvec, and the agreement of the two
+    fp64_ms = None
+    parity = None
+    if prec != sm.SMASH_PREC_F64:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = step(precision=sm.SMASH_PREC_F64)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+        z64 = z.clone()
+        sm.smash_matvec_ex(h, q, z, prec, stream=stream)
+        torch.cuda.synchronize()
+        parity = float(torch.linalg.norm(z - z64) / torch.linalg.norm(z64))
+        sm.smash_free(h)
     sm.smash_set_profiling(False)
 
     if rank != 0:
@@ -246,27 +270,42 @@ def bench_ours(args, w):
         return
     peaks, peak_src = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak_tflops = NUM_SMS * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     nrhs = w["nrhs"]
-    cpl_flops = info["coupling_pairs"] * (2 * nrhs + PAIR_EVAL_FLOPS)
     cpl_ms = statistics.mean(coupling_ms)
-    achieved = cpl_flops / (cpl_ms / 1e3) / 1e12
+    if prec == sm.SMASH_PREC_F64:
+        peak = NUM_SMS * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        cpl_work = info["coupling_pairs"] * (2 * nrhs + PAIR_EVAL_FLOPS)
+        kname = "coupling (ksum_f64_kernel over L)"
+        psrc = (f"FP64 {FP64_FLOPS_PER_CLK_SM} flop/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                "(nominal unit count, sampled clock; an FMA probe measured 1.19 TFLOP/s)")
+        wdef = f"per kernel entry 2*nrhs + {PAIR_EVAL_FLOPS} FP64 flops"
+    else:
+        peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        cpl_work = info["coupling_pairs"] * (DD_MAC_OPS * nrhs + DD_EVAL_OPS)
+        kname = "coupling (ksum_dd_kernel over L, double-float on the FP32 pipe)"
+        psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                "(one FMA = one operation)")
+        wdef = (f"per kernel entry {DD_MAC_OPS}*nrhs + {DD_EVAL_OPS} FP32 instructions of the "
+                "double-float algorithm (error-free products and sums)")
+    achieved = cpl_work / (cpl_ms / 1e3) / 1e12
     cpu = run_cpu_oracle(CPU_SAMPLE_N, w) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if prec != sm.SMASH_PREC_F64 else "f64",
+        "data": "synthetic",
         "config": {"workload": "3d_invr uniform cube N=2^20" if n == 1 << 20 else f"3d_invr uniform cube N={n}",
                    "n": n, "dim": 3, "kernel": "1/|x-y|",
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
-                   "precision": "fp64", "l2": "flushed (256 MiB write) before every timed step",
+                   "precision": "build fp64; matvec " + ("fp64" if prec == sm.SMASH_PREC_F64 else
+                                                          "double-float kernel sums, fp64 transfers"),
+                   "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{ws}"},
-        "roofline": {"bound": "alu", "kernel": "coupling (ksum_f64_kernel over L)",
-                     "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak_tflops, "traffic": None,
-                     "peak_source": f"FP64 {FP64_FLOPS_PER_CLK_SM} flop/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
-                                    "(nominal unit count, sampled clock)",
-                     "flops_per_launch": cpl_flops, "ms_per_launch": cpl_ms},
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": psrc, "work_definition": wdef,
+                     "work_per_launch": cpl_work, "ms_per_launch": cpl_ms},
+        "fp64_matvec_step": None if fp64_ms is None else {"ms_per_step": fp64_ms, "value": ws * n / (fp64_ms / 1e3)},
+        "rel_diff_vs_fp64_matvec": parity,
         "phases_ms": phases,
         "structure": {k: info[k] for k in ("levels", "nnodes", "nadm", "nnear", "skel_row", "g_row",
                                            "coupling_pairs", "near_pairs", "swaps")},
@@ -295,6 +334,8 @@ def main():
     ap.add_argument("--workload", default="3d_invr_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe); for profiling cases")
+    ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64"],
+                    help="matvec arithmetic: double-float kernel sums (FP64-accurate) or plain FP64")
     args = ap.parse_args()
     w = dict(si.WORKLOADS[args.workload])
     if args.n:

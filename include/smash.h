@@ -61,9 +61,13 @@ enum {
     SMASH_K_CAUCHY1D = 3 /* 1 / (x - y), dim = 1, (6.1) */
 };
 
-/* Arithmetic of the matvec products (Section 3.4).  The build is FP64. */
+/* Arithmetic of the matvec (Section 3.4).  The build is always FP64. */
 enum {
-    SMASH_PREC_F64 = 0  /* FP64 kernel evaluation, transfers and sums */
+    SMASH_PREC_F64 = 0,   /* FP64 kernel evaluation, transfers and sums */
+    SMASH_PREC_F32X2 = 1  /* coupling and near field in double-float arithmetic on the FP32
+                             pipe (each value hi + lo floats, error-free products and sums,
+                             ~1e-12 relative to FP64); transfers FP64.  Kernels 1/|x-y| and
+                             1/(x-y) only. */
 };
 
 typedef struct {
@@ -118,9 +122,10 @@ SMASH_API smash_status smash_matvec(smash_handle h, const double *X, double *Y, 
 
 /*
  * smash_matvec_ex -- as smash_matvec with a precision mode (SMASH_PREC_*)
- * and a cudaStream_t (NULL = the handle's stream).  Asynchronous with
- * respect to the host when X and Y are device memory; with host buffers it
- * returns after the result has been copied back.
+ * and a cudaStream_t.  stream == NULL: runs on the handle's stream and
+ * returns when Y is complete (like smash_matvec).  An explicit stream: the
+ * work is queued on it and the call returns without waiting when X and Y are
+ * device memory; with host buffers it returns after Y has been copied back.
  */
 SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision,
                              void *stream);

@@ -234,6 +234,43 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
         build_lists(h, scratch);
         tm.mark();
         build_compression(h, scratch);
+        if (dd_supported(h->kernel_id)) {
+            // double-float copies of the point and skeleton coordinates for the
+            // SMASH_PREC_F32X2 matvec
+            h->xs_dd = h->mem.alloc<float>((size_t)h->nx * 8);
+            dd_coords(h->xs, h->nx, h->lo, h->s, h->xs_dd, h->stream);
+            if (h->same) {
+                h->ys_dd = h->xs_dd;
+            } else {
+                h->ys_dd = h->mem.alloc<float>((size_t)h->ny * 8);
+                dd_coords(h->ys, h->ny, h->lo, h->s, h->ys_dd, h->stream);
+            }
+            h->row.skel_dd = h->mem.alloc<float>((size_t)std::max<int64_t>(h->row.total_skel, 1) * 8);
+            dd_coords(h->row.skel_xyz, h->row.total_skel, h->lo, h->s, h->row.skel_dd, h->stream);
+            if (!h->same) {
+                h->colside.skel_dd = h->mem.alloc<float>((size_t)std::max<int64_t>(h->colside.total_skel, 1) * 8);
+                dd_coords(h->colside.skel_xyz, h->colside.total_skel, h->lo, h->s, h->colside.skel_dd, h->stream);
+            }
+            // exact three-float copies: points (near field) and, for deep trees, skeletons
+            h->dd_e = dd_exact_exponent(h->s);
+            h->xs_x3 = h->mem.alloc<float>((size_t)h->nx * 12);
+            dd_coords3(h->xs, h->nx, h->dd_e, h->xs_x3, h->stream);
+            if (h->same) {
+                h->ys_x3 = h->xs_x3;
+            } else {
+                h->ys_x3 = h->mem.alloc<float>((size_t)h->ny * 12);
+                dd_coords3(h->ys, h->ny, h->dd_e, h->ys_x3, h->stream);
+            }
+            if (h->L > kDdNormalisedMaxLevels) {
+                h->row.skel_x3 = h->mem.alloc<float>((size_t)std::max<int64_t>(h->row.total_skel, 1) * 12);
+                dd_coords3(h->row.skel_xyz, h->row.total_skel, h->dd_e, h->row.skel_x3, h->stream);
+                if (!h->same) {
+                    h->colside.skel_x3 =
+                        h->mem.alloc<float>((size_t)std::max<int64_t>(h->colside.total_skel, 1) * 12);
+                    dd_coords3(h->colside.skel_xyz, h->colside.total_skel, h->dd_e, h->colside.skel_x3, h->stream);
+                }
+            }
+        }
         tm.mark();
         tm.finish(0);
         build_stats(h, scratch);
@@ -257,7 +294,10 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         if (!h) fail(SMASH_EINVAL, "handle is NULL");
         if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
         if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
-        if (precision != SMASH_PREC_F64) fail(SMASH_EINVAL, "unknown precision %d", precision);
+        if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2)
+            fail(SMASH_EINVAL, "unknown precision %d", precision);
+        if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
+            fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
         cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
         Arena io(s);
         const double *Xd = X;
@@ -270,12 +310,13 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         }
         if (yhost) Yd = io.alloc<double>((size_t)h->nx * nrhs);
         h->prof_mv.on = profiling_enabled();
-        matvec_f64(h, Xd, Yd, nrhs, s, &h->prof_mv);
-        if (yhost) {
-            CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
+        if (precision == SMASH_PREC_F32X2)
+            matvec_dd(h, Xd, Yd, nrhs, s, &h->prof_mv);
+        else
+            matvec_f64(h, Xd, Yd, nrhs, s, &h->prof_mv);
+        if (yhost) CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         io.release();
+        if (yhost || !stream) CK(cudaStreamSynchronize(s));
         return SMASH_OK;
     } catch (const Error &e) {
         return record(e);
@@ -286,14 +327,7 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
 }
 
 smash_status smash_matvec(smash_handle h, const double *X, double *Y, int nrhs) {
-    smash_status st = smash_matvec_ex(h, X, Y, nrhs, SMASH_PREC_F64, nullptr);
-    if (st != SMASH_OK) return st;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        t_last_error = cudaGetErrorString(e);
-        return SMASH_ECUDA;
-    }
-    return SMASH_OK;
+    return smash_matvec_ex(h, X, Y, nrhs, SMASH_PREC_F64, nullptr);
 }
 
 void smash_free(smash_handle h) { destroy(h); }

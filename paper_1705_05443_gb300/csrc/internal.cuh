@@ -91,6 +91,8 @@ struct Side {
     double *G = nullptr;
     int64_t *skel_gidx = nullptr; // per skeleton slot: sorted point index
     double *skel_xyz = nullptr;   // per skeleton slot: coordinates, stride 4
+    float *skel_dd = nullptr;     // per skeleton slot: double-float normalised coordinates, 8 floats
+    float *skel_x3 = nullptr;     // per skeleton slot: exact three-float coordinates, 12 floats (deep trees)
     int64_t total_skel = 0, total_loc = 0, total_g = 0, skel_cap = 0;
     std::vector<int64_t> mub_max;  // per level, upper bound of m
 };
@@ -116,6 +118,9 @@ struct smash_h2 {
     int64_t *permx = nullptr, *permy = nullptr;
     uint64_t *keyx = nullptr, *keyy = nullptr;
     double *xs = nullptr, *ys = nullptr;  // stride 4
+    float *xs_dd = nullptr, *ys_dd = nullptr;  // double-float x'' = 1 + (x - lo)/s, 8 floats per point
+    float *xs_x3 = nullptr, *ys_x3 = nullptr;  // exact three-float x 2^-dd_e, 12 floats per point
+    int dd_e = 0;
     // tree
     int L = 0;
     std::vector<int64_t> lvl_off;  // host copy, L + 1 entries
@@ -151,6 +156,19 @@ void build_stats(smash_h2 *h, Arena &scratch);
 // matvec in FP64: X_dev (ny x nrhs), Y_dev (nx x nrhs), both device
 void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
                 Profile *prof);
+// matvec with double-float kernel sums (kernels 1/|x-y| and 1/(x-y))
+void matvec_dd(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
+bool dd_supported(int kernel_id);
+void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
+void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
+int dd_exact_exponent(double s);
+// the double-float coupling uses normalised two-float coordinates up to this depth
+constexpr int kDdNormalisedMaxLevels = 10;
+// pass helpers shared by the matvec variants
+void matvec_gather(const smash_h2 *h, const double *X, int nrhs, int ldq, double *qs, cudaStream_t s);
+void matvec_upward(const smash_h2 *h, const double *qs, double *qhat, int ldq, cudaStream_t s);
+void matvec_downward(const smash_h2 *h, double *zhat, double *zs, int ldq, cudaStream_t s);
+void matvec_scatter(const smash_h2 *h, const double *zs, int ldq, int nrhs, double *Y, cudaStream_t s);
 
 // The same matvec with caller-provided device scratch (no allocation):
 // matvec_f64_scratch_bytes is the scratch it needs for nrhs right-hand sides.

@@ -307,6 +307,41 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
     tmp.release();
 }
 
+// ------------------------------------------------------------------ pass helpers
+// The gather, transfer and scatter passes of matvec_f64 as separate calls,
+// shared by the double-float matvec.
+void matvec_gather(const smash_h2 *h, const double *X, int nrhs, int ldq, double *qs, cudaStream_t s) {
+    gather_rhs_kernel<<<(unsigned)((h->ny * ldq + 255) / 256), 256, 0, s>>>(X, nrhs, h->permy, h->ny, ldq, qs);
+    LAUNCHED();
+}
+
+void matvec_upward(const smash_h2 *h, const double *qs, double *qhat, int ldq, cudaStream_t s) {
+    const Side &Cs = *h->col;
+    for (int l = h->L; l >= 2; --l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassArgs p{n0, h->leaf, Cs.m, Cs.k, Cs.in_off, Cs.sk_off, Cs.loc_off, Cs.g_off, Cs.loc, Cs.G,
+                   qs, qhat, qhat, nullptr, ldq};
+        upward_kernel<<<(unsigned)nl, 256, 0, s>>>(p);
+        LAUNCHED();
+    }
+}
+
+void matvec_downward(const smash_h2 *h, double *zhat, double *zs, int ldq, cudaStream_t s) {
+    const Side &R = h->row;
+    for (int l = 2; l <= h->L; ++l) {
+        int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassArgs p{n0, h->leaf, R.m, R.k, R.in_off, R.sk_off, R.loc_off, R.g_off, R.loc, R.G,
+                   nullptr, zhat, zhat, zs, ldq};
+        downward_kernel<<<(unsigned)nl, 256, 0, s>>>(p);
+        LAUNCHED();
+    }
+}
+
+void matvec_scatter(const smash_h2 *h, const double *zs, int ldq, int nrhs, double *Y, cudaStream_t s) {
+    scatter_rhs_kernel<<<(unsigned)((h->nx * nrhs + 255) / 256), 256, 0, s>>>(zs, ldq, h->permx, h->nx, nrhs, Y);
+    LAUNCHED();
+}
+
 // ------------------------------------------------------------------ caller scratch
 // The passes of matvec_f64 with qs, zs, q^ and z^ carved out of a caller
 // buffer instead of stream-ordered allocations.  Every carved region is

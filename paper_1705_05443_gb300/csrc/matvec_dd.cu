@@ -1,0 +1,421 @@
+// matvec_dd.cu -- the Section 3.4 matvec with the coupling (3.19) and the
+// near field (3.20) in double-float arithmetic on the FP32 pipe.
+//
+// GB300 executes FP32 FMA ~61x faster than FP64 FMA, and the FP64 kernel-sum
+// kernel saturates the FP64 pipe.  Here every value of the kernel sums is an
+// unevaluated sum of two floats (hi + lo, ~48-bit significand) and every
+// operation is an error-free transformation (Knuth's TwoSum, Dekker's
+// product via FMA), so the result keeps FP64-class accuracy (~1e-12 relative
+// against the FP64 oracle) while running on the FP32 pipe.
+//
+//  * Coordinates, two representations:
+//    - normalised: x'' = 1 + (x - lo)/s in [1, 2) split into (hi, lo) floats.
+//      Two hi parts in [1, 2] differ by an exactly representable float
+//      (Sterbenz), so a difference is hi_a - hi_b (exact) plus lo_a - lo_b,
+//      with an absolute error ~2^-48.  Used for the coupling of trees with at
+//      most 10 levels, where admissible pairs are at least ~0.4 cell widths
+//      apart and the relative error stays below ~5e-12.
+//    - exact: x~ = x 2^-e (a power-of-two scaling, exact) split into three
+//      floats hi + mid + lo that represent the FP64 value exactly; differences
+//      by TwoDiff on hi and mid parts carry ~2^-48 relative precision however
+//      close the points are (FP64 subtracts close points exactly too).  Used
+//      for the near field and for the coupling of deeper trees.
+//    The kernel is evaluated in these units and the sums are scaled at the
+//    end: 1/|x - y| = (1/s) / |x'' - y''| = 2^-e / |x~ - y~|, and likewise
+//    1/(x - y) in 1D.
+//  * 1/sqrt(r2): hardware reciprocal square root of hi(r2) as the seed, then
+//    one Newton step y1 = y0 + y0 (1 - r2 y0^2) / 2 in double-float
+//    (relative error ~3 eps_f^2 / 8 ~ 2e-14).  1/d in 1D: reciprocal seed and
+//    one Newton step y1 = y0 + y0 (1 - d y0).
+//  * q vectors are split into (hi, lo) floats by a conversion pass; the
+//    accumulators are double-float pairs renormalised after every source
+//    tile, and written out in FP64.
+// Compiled with --fmad=false: every fused operation below is an explicit fmaf.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace smash {
+
+// ------------------------------------------------------------------ error-free transforms
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+// ------------------------------------------------------------------ conversions
+// per point: (hi x, hi y, hi z, 0, lo x, lo y, lo z, 0) of x'' = 1 + (x - lo)/s
+__global__ void dd_coords_kernel(const double *__restrict__ pts, int64_t n, double lo0, double lo1, double lo2,
+                                 double s, float *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double lo[3] = {lo0, lo1, lo2};
+    float hi[4] = {0, 0, 0, 0}, lw[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        double v = 1.0 + (pts[i * 4 + a] - lo[a]) / s;
+        float h = __double2float_rn(v);
+        hi[a] = h;
+        lw[a] = __double2float_rn(v - (double)h);
+    }
+    float4 *o = reinterpret_cast<float4 *>(out + i * 8);
+    o[0] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    o[1] = make_float4(lw[0], lw[1], lw[2], 0.f);
+}
+
+// per point: three float4 (hi, mid, lo) of x~ = x 2^-e; hi + mid + lo == x~ exactly
+__global__ void dd_coords3_kernel(const double *__restrict__ pts, int64_t n, int e, float *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[3] = {0, 0, 0}, m[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        double v = ldexp(pts[i * 4 + a], -e);
+        h[a] = __double2float_rn(v);
+        double r = v - (double)h[a];
+        m[a] = __double2float_rn(r);
+        l[a] = __double2float_rn(r - (double)m[a]);
+    }
+    float4 *o = reinterpret_cast<float4 *>(out + i * 12);
+    o[0] = make_float4(h[0], h[1], h[2], 0.f);
+    o[1] = make_float4(m[0], m[1], m[2], 0.f);
+    o[2] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// (hi, lo) float pairs of FP64 values
+__global__ void dd_split_kernel(const double *__restrict__ in, int64_t n, float2 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = in[i];
+    float h = __double2float_rn(v);
+    out[i] = make_float2(h, __double2float_rn(v - (double)h));
+}
+
+bool dd_supported(int kernel_id) { return kernel_id == SMASH_K_INVR || kernel_id == SMASH_K_CAUCHY1D; }
+
+void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st) {
+    if (n <= 0) return;
+    dd_coords_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, n, lo[0], lo[1], lo[2], s, out);
+    LAUNCHED();
+}
+
+void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st) {
+    if (n <= 0) return;
+    dd_coords3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, n, e, out);
+    LAUNCHED();
+}
+
+int dd_exact_exponent(double s) { return ilogb(s); }
+
+static void dd_split(const double *in, int64_t n, float2 *out, cudaStream_t st) {
+    if (n <= 0) return;
+    dd_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, out);
+    LAUNCHED();
+}
+
+// ------------------------------------------------------------------ differences
+// x - y from three-float coordinates, as a normalised double-float
+__device__ __forceinline__ void diff3(float xh, float xm, float xl, float yh, float ym, float yl, float &dh,
+                                      float &dl) {
+    float a, ea, b, eb;
+    two_sum(xh, -yh, a, ea);
+    two_sum(xm, -ym, b, eb);
+    float c = xl - yl;
+    float s, t;
+    two_sum(a, b, s, t);
+    t = t + ((ea + eb) + c);
+    fast_two_sum(s, t, dh, dl);
+}
+
+// ------------------------------------------------------------------ kernel entries
+// kappa'' = 1/|d| (3D/2D/1D) or 1/d (Cauchy, 1D) in double-float; d = (dh + dl) per axis.
+template <int KID, int D>
+__device__ __forceinline__ void kappa_dd(const float *dh, const float *dl, float &kh, float &kl) {
+    if (KID == SMASH_K_CAUCHY1D) {
+        float h = dh[0], l = dl[0];
+        float dsum, derr;
+        fast_two_sum(h, l, dsum, derr);  // |h| >= |l| unless h == 0
+        if (dsum == 0.f && derr == 0.f) { kh = 0.f; kl = 0.f; return; }
+        float y0 = __frcp_rn(dsum);
+        float uh = dsum * y0;
+        float ul = fmaf(dsum, y0, -uh);
+        ul = fmaf(derr, y0, ul);
+        float ee = (1.0f - uh) - ul;
+        float c = y0 * ee;
+        fast_two_sum(y0, c, kh, kl);
+        return;
+    }
+    // r2 = sum_a (dh + dl)^2 as a double-float
+    float p[3], e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            p[a] = dh[a] * dh[a];
+            float t = fmaf(dh[a], dh[a], -p[a]);
+            t = fmaf(2.0f * dh[a], dl[a], t);
+            e[a] = fmaf(dl[a], dl[a], t);
+        } else {
+            p[a] = 0.f;
+            e[a] = 0.f;
+        }
+    }
+    float s1, t1, rh, t2;
+    two_sum(p[0], p[1], s1, t1);
+    two_sum(s1, p[2], rh, t2);
+    float rl = ((e[0] + e[1]) + (e[2] + t1)) + t2;
+    fast_two_sum(rh, rl, rh, rl);
+    if (rh == 0.f) { kh = 0.f; kl = 0.f; return; }
+    float y0 = rsqrtf(rh);
+    float th = y0 * y0;
+    float tl = fmaf(y0, y0, -th);
+    float uh = rh * th;
+    float ul = fmaf(rh, th, -uh);
+    ul = fmaf(rh, tl, ul);
+    ul = fmaf(rl, th, ul);
+    float ee = (1.0f - uh) - ul;
+    float c = y0 * (0.5f * ee);
+    fast_two_sum(y0, c, kh, kl);
+}
+
+// ------------------------------------------------------------------ kernel sums
+struct KsumDDArgs {
+    const int32_t *tnodes;
+    const int64_t *t_off;
+    const int32_t *t_cnt;
+    const int64_t *ptr;
+    const int32_t *col;
+    const int64_t *s_off;
+    const int32_t *s_cnt;
+    const float *xt;   // target coordinates, 8 floats per point
+    const float *ys;   // source coordinates, 8 floats per point
+    const float2 *qv;  // source vectors as (hi, lo), ldq per point
+    double *out;       // target vectors (FP64), ldq
+    double scale;      // 1/s
+    int ldq, nchunks, tbp, groups;
+};
+
+constexpr int kDdThreads = 256;
+constexpr int kDdTile = 128;
+
+template <int KID, int D, int RC, bool EXACT>
+__global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int NC = EXACT ? 3 : 2;                                 // float4 per point
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // kDdTile * NC
+    float2 *sq = reinterpret_cast<float2 *>(sy + NC * kDdTile);      // kDdTile * ldq
+    double *red = reinterpret_cast<double *>(sq + (size_t)kDdTile * a.ldq);  // tbp * ldq
+    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);
+
+    const int64_t g = a.tnodes[blockIdx.x];
+    const int T = a.t_cnt[g];
+    if (T == 0) return;
+    const int64_t toff = a.t_off[g];
+    const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
+    const int ldq = a.ldq;
+    const int tid = threadIdx.x;
+    const int per_group = a.tbp * a.nchunks;
+    const int grp = tid / per_group;
+    const int lt = tid % per_group;
+    const int ta = lt % a.tbp;
+    const int ch = lt / a.tbp;
+    const bool active = grp < a.groups;
+
+    for (int tb = 0; tb < T; tb += a.tbp) {
+        const int tcount = min(a.tbp, T - tb);
+        const bool have = active && ta < tcount;
+        float4 xc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (have) {
+            const float4 *xp = reinterpret_cast<const float4 *>(a.xt + (toff + tb + ta) * (4 * NC));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) xc[c] = xp[c];
+        }
+        float ah[RC], al[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) { ah[r] = 0.f; al[r] = 0.f; }
+        int64_t e = e0;
+        int off = 0;
+        while (e < e1) {
+            int fill = 0;
+            while (e < e1 && fill < kDdTile) {
+                int j = a.col[e];
+                int S = a.s_cnt[j];
+                int take = min(S - off, kDdTile - fill);
+                int64_t so = a.s_off[j] + off;
+                for (int q = tid; q < take; q += kDdThreads) sidx[fill + q] = so + q;
+                fill += take;
+                off += take;
+                if (off >= S) { ++e; off = 0; }
+            }
+            __syncthreads();
+            for (int q = tid; q < fill * NC; q += kDdThreads) {
+                int b = q / NC, c = q % NC;
+                sy[c * kDdTile + b] = reinterpret_cast<const float4 *>(a.ys + sidx[b] * (4 * NC))[c];
+            }
+            for (int q = tid; q < fill * ldq; q += kDdThreads) {
+                int b = q / ldq, c = q % ldq;
+                sq[q] = a.qv[sidx[b] * ldq + c];
+            }
+            __syncthreads();
+            if (have) {
+                for (int b = grp; b < fill; b += a.groups) {
+                    float dh[3], dl[3];
+                    if (EXACT) {
+                        float4 yh = sy[b], ym = sy[kDdTile + b], yl = sy[2 * kDdTile + b];
+                        diff3(xc[0].x, xc[1].x, xc[2 % NC].x, yh.x, ym.x, yl.x, dh[0], dl[0]);
+                        diff3(xc[0].y, xc[1].y, xc[2 % NC].y, yh.y, ym.y, yl.y, dh[1], dl[1]);
+                        diff3(xc[0].z, xc[1].z, xc[2 % NC].z, yh.z, ym.z, yl.z, dh[2], dl[2]);
+                    } else {
+                        float4 yh = sy[b], yl = sy[kDdTile + b];
+                        dh[0] = xc[0].x - yh.x; dh[1] = xc[0].y - yh.y; dh[2] = xc[0].z - yh.z;
+                        dl[0] = xc[1].x - yl.x; dl[1] = xc[1].y - yl.y; dl[2] = xc[1].z - yl.z;
+                    }
+                    float kh, kl;
+                    kappa_dd<KID, D>(dh, dl, kh, kl);
+                    const float2 *qb = sq + (size_t)b * ldq + ch * RC;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        float2 qq = qb[r];
+                        float p = kh * qq.x;
+                        float pe = fmaf(kh, qq.x, -p);
+                        pe = fmaf(kh, qq.y, pe);
+                        pe = fmaf(kl, qq.x, pe);
+                        float s, t;
+                        two_sum(ah[r], p, s, t);
+                        ah[r] = s;
+                        al[r] = al[r] + (t + pe);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RC; ++r) fast_two_sum(ah[r], al[r], ah[r], al[r]);
+            }
+            __syncthreads();
+        }
+        for (int gg = 0; gg < a.groups; ++gg) {
+            if (have && grp == gg) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    double v = (double)ah[r] + (double)al[r];
+                    double *dst = red + (size_t)ta * ldq + ch * RC + r;
+                    *dst = gg == 0 ? v : *dst + v;
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < tcount * ldq; q += kDdThreads) a.out[(toff + tb) * ldq + q] = red[q] * a.scale;
+        __syncthreads();
+    }
+}
+
+template <int KID, int D, bool EXACT>
+static void launch_dd(KsumDDArgs a, int64_t ntn, int RC, cudaStream_t s) {
+    if (ntn <= 0) return;
+    constexpr int NC = EXACT ? 3 : 2;
+    size_t smem = sizeof(float4) * NC * kDdTile + sizeof(float2) * (size_t)kDdTile * a.ldq +
+                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * kDdTile;
+    void (*kern)(KsumDDArgs) = nullptr;
+    switch (RC) {
+    case 1: kern = ksum_dd_kernel<KID, D, 1, EXACT>; break;
+    case 2: kern = ksum_dd_kernel<KID, D, 2, EXACT>; break;
+    case 4: kern = ksum_dd_kernel<KID, D, 4, EXACT>; break;
+    case 8: kern = ksum_dd_kernel<KID, D, 8, EXACT>; break;
+    case 16: kern = ksum_dd_kernel<KID, D, 16, EXACT>; break;
+    default: kern = ksum_dd_kernel<KID, D, 32, EXACT>; break;
+    }
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)ntn, kDdThreads, smem, s>>>(a);
+    LAUNCHED();
+}
+
+template <bool EXACT>
+static void ksum_dd_dispatch(int kid, int dim, KsumDDArgs a, int64_t ntn, int RC, cudaStream_t s) {
+    if (kid == SMASH_K_CAUCHY1D) {
+        launch_dd<SMASH_K_CAUCHY1D, 1, EXACT>(a, ntn, RC, s);
+    } else if (dim == 3) {
+        launch_dd<SMASH_K_INVR, 3, EXACT>(a, ntn, RC, s);
+    } else if (dim == 2) {
+        launch_dd<SMASH_K_INVR, 2, EXACT>(a, ntn, RC, s);
+    } else {
+        launch_dd<SMASH_K_INVR, 1, EXACT>(a, ntn, RC, s);
+    }
+}
+
+static void ksum_dd(int kid, int dim, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
+                    cudaStream_t s) {
+    a.nchunks = a.ldq / RC;
+    int tbp = 32;
+    while (tbp < max_targets && tbp * 2 * a.nchunks <= kDdThreads) tbp *= 2;
+    if (tbp * a.nchunks > kDdThreads) tbp = std::max(1, kDdThreads / a.nchunks);
+    a.tbp = tbp;
+    a.groups = std::max(1, kDdThreads / (tbp * a.nchunks));
+    if (exact)
+        ksum_dd_dispatch<true>(kid, dim, a, ntn, RC, s);
+    else
+        ksum_dd_dispatch<false>(kid, dim, a, ntn, RC, s);
+}
+
+// ------------------------------------------------------------------ transfers (FP64)
+// The upward and downward passes are HBM-bound and stay in FP64.
+void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof) {
+    const Side &R = h->row;
+    const Side &Cs = *h->col;
+    int ldq, RC;
+    if (nrhs <= 32) {
+        RC = 1;
+        while (RC < nrhs) RC *= 2;
+        ldq = RC;
+    } else {
+        RC = 32;
+        ldq = (nrhs + 31) / 32 * 32;
+    }
+    Arena tmp(s);
+    double *qs = tmp.alloc<double>((size_t)h->ny * ldq);
+    double *zs = tmp.alloc<double>((size_t)h->nx * ldq);
+    double *qhat = tmp.alloc<double>((size_t)std::max<int64_t>(Cs.total_skel, 1) * ldq);
+    double *zhat = tmp.alloc<double>((size_t)std::max<int64_t>(R.total_skel, 1) * ldq);
+    float2 *qs2 = tmp.alloc<float2>((size_t)h->ny * ldq);
+    float2 *qhat2 = tmp.alloc<float2>((size_t)std::max<int64_t>(Cs.total_skel, 1) * ldq);
+    const double scale = 1.0 / h->s;
+    PhaseTimer tm(s, prof);
+    tm.mark();
+    matvec_gather(h, X, nrhs, ldq, qs, s);
+    dd_split(qs, h->ny * ldq, qs2, s);
+    tm.mark();
+    {
+        KsumDDArgs a{};
+        a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
+        a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
+        a.xt = h->xs_x3; a.ys = h->ys_x3; a.qv = qs2; a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq;
+        ksum_dd(h->kernel_id, h->dim, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+    }
+    tm.mark();
+    matvec_upward(h, qs, qhat, ldq, s);
+    dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
+    tm.mark();
+    if (h->nnodes > 1) {
+        KsumDDArgs a{};
+        a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
+        a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
+        const bool exact = h->L > kDdNormalisedMaxLevels;
+        a.xt = exact ? R.skel_x3 : R.skel_dd;
+        a.ys = exact ? Cs.skel_x3 : Cs.skel_dd;
+        a.qv = qhat2; a.out = zhat; a.scale = exact ? ldexp(1.0, -h->dd_e) : scale; a.ldq = ldq;
+        ksum_dd(h->kernel_id, h->dim, exact, a, h->nnodes - 1, h->r, RC, s);
+    }
+    tm.mark();
+    matvec_downward(h, zhat, zs, ldq, s);
+    tm.mark();
+    matvec_scatter(h, zs, ldq, nrhs, Y, s);
+    tm.mark();
+    tm.finish(4);
+    tmp.release();
+}
+
+}  // namespace smash
