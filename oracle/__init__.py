@@ -90,7 +90,9 @@ def _load():
         lib.orc_chebyshev.argtypes = [i32, P]
         lib.orc_chebyshev.restype = None
         lib.orc_lagrange.restype = dbl
-        lib.orc_lagrange.argtypes = [i32, P, i32, dbl]
+        lib.orc_lagrange.argtypes = [i32, P, P, i32, dbl]
+        lib.orc_lagrange_weights.restype = None
+        lib.orc_lagrange_weights.argtypes = [i32, P, P]
         lib.orc_basis_t.argtypes = [i32, i32, P, P, dbl, i32, P, P, i32, P]
         lib.orc_basis_t.restype = None
         lib.orc_compr.restype = i32
@@ -182,7 +184,9 @@ def chebyshev(p: int) -> np.ndarray:
 
 def lagrange(p: int, m: int, t: float, anchors=None) -> float:
     anchors = chebyshev(p) if anchors is None else _f64(anchors)
-    return _load().orc_lagrange(p, _ptr(anchors), m, float(t))
+    w = np.empty(p)
+    _load().orc_lagrange_weights(p, _ptr(anchors), _ptr(w))
+    return _load().orc_lagrange(p, _ptr(anchors), _ptr(w), m, float(t))
 
 
 def basis_t(pts, p: int, lo, s: float, level: int, cell, anchors=None) -> np.ndarray:

@@ -27,7 +27,9 @@
  * stopped at |R_jj| <= tol |R_00|, followed by Gu-Eisenstat swaps until
  * max_ij (A_ij^2 + gamma_j^2 / omega_i^2) <= f^2.
  *
- * Compile with -ffp-contract=off: every a*b+c below is two rounded operations.
+ * Compile with -ffp-contract=off: a*b+c below is two rounded operations unless
+ * it is written as fma(a, b, c), the IEEE fused multiply-add (one rounding);
+ * the dot products, norms and triangular solves use fma.
  */
 #include <math.h>
 #include <stdint.h>
@@ -246,16 +248,24 @@ void orc_chebyshev(int p, double *t)
         t[m] = cos((double)(2 * m + 1) * ORC_PI / (double)(2 * p));
 }
 
-/* ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n). */
-double orc_lagrange(int p, const double *anchors, int m, double t)
+/* Weights of the Lagrange polynomials of the anchors:
+ * w_m = 1 / prod_{n != m} (t_m - t_n). */
+void orc_lagrange_weights(int p, const double *anchors, double *w)
 {
-    double v = 1.0;
-    for (int n = 0; n < p; ++n) {
-        if (n == m) continue;
-        double num = t - anchors[n];
-        double den = anchors[m] - anchors[n];
-        v = v * (num / den);
+    for (int m = 0; m < p; ++m) {
+        double den = 1.0;
+        for (int n = 0; n < p; ++n)
+            if (n != m) den = den * (anchors[m] - anchors[n]);
+        w[m] = 1.0 / den;
     }
+}
+
+/* ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n) = w_m prod_{n != m} (t - t_n). */
+double orc_lagrange(int p, const double *anchors, const double *w, int m, double t)
+{
+    double v = w[m];
+    for (int n = 0; n < p; ++n)
+        if (n != m) v = v * (t - anchors[n]);
     return v;
 }
 
@@ -271,13 +281,14 @@ void orc_basis_t(int d, int p, const double *anchors, const double *lo, double s
     double half = 0.5 * h;
     int r = 1;
     for (int a = 0; a < d; ++a) r *= p;
-    double L[3][ORC_MAXP];
+    double L[3][ORC_MAXP], wts[ORC_MAXP];
+    orc_lagrange_weights(p, anchors, wts);
     for (int c = 0; c < npts; ++c) {
         for (int a = 0; a < d; ++a) {
             double centre = lo[a] + ((double)cell[a] + 0.5) * h;
             double t = (pts[c * d + a] - centre) / half;
             for (int m = 0; m < p; ++m)
-                L[a][m] = orc_lagrange(p, anchors, m, t);
+                L[a][m] = orc_lagrange(p, anchors, wts, m, t);
         }
         for (int kk = 0; kk < r; ++kk) {
             int rem = kk, idx[3] = {0, 0, 0};
@@ -302,11 +313,11 @@ static void orc_householder(double *W, int r, int m, int j, double *v)
     double sigma = 0.0;
     for (int i = j + 1; i < r; ++i) {
         double x = W[(size_t)i * m + j];
-        sigma = sigma + x * x;
+        sigma = fma(x, x, sigma);
     }
     if (sigma == 0.0)
         return; /* already triangular in this column: H = I */
-    double nrm = sqrt(alpha * alpha + sigma);
+    double nrm = sqrt(fma(alpha, alpha, sigma));
     double beta = alpha <= 0.0 ? nrm : -nrm;
     double tau = (beta - alpha) / beta;
     double den = alpha - beta;
@@ -316,11 +327,11 @@ static void orc_householder(double *W, int r, int m, int j, double *v)
     for (int c = j + 1; c < m; ++c) {
         double w = W[(size_t)j * m + c];
         for (int i = j + 1; i < r; ++i)
-            w = w + v[i] * W[(size_t)i * m + c];
+            w = fma(v[i], W[(size_t)i * m + c], w);
         double tw = tau * w;
         W[(size_t)j * m + c] = W[(size_t)j * m + c] - tw;
         for (int i = j + 1; i < r; ++i)
-            W[(size_t)i * m + c] = W[(size_t)i * m + c] - tw * v[i];
+            W[(size_t)i * m + c] = fma(-tw, v[i], W[(size_t)i * m + c]);
     }
     W[(size_t)j * m + j] = beta;
     for (int i = j + 1; i < r; ++i)
@@ -342,7 +353,7 @@ static int orc_qr(double *W, int r, int m, int *perm, int pivot, int ksteps, dou
                 double s2 = 0.0;
                 for (int i = j; i < r; ++i) {
                     double x = W[(size_t)i * m + c];
-                    s2 = s2 + x * x;
+                    s2 = fma(x, x, s2);
                 }
                 nrm2[c] = s2;
             }
@@ -396,7 +407,7 @@ int orc_compr(const double *Mt, int r, int m, double tol, double f, int *perm, i
             for (int t = k - 1; t >= 0; --t) {
                 double s = W[(size_t)t * m + k + u];
                 for (int q = t + 1; q < k; ++q)
-                    s = s - W[(size_t)t * m + q] * A[(size_t)q * mk + u];
+                    s = fma(-W[(size_t)t * m + q], A[(size_t)q * mk + u], s);
                 A[(size_t)t * mk + u] = s / W[(size_t)t * m + t];
             }
         /* X = R11^{-1}; 1/omega_t^2 = squared norm of row t of X */
@@ -404,14 +415,14 @@ int orc_compr(const double *Mt, int r, int m, double tol, double f, int *perm, i
             for (int t = k - 1; t >= 0; --t) {
                 double s = (t == c) ? 1.0 : 0.0;
                 for (int q = t + 1; q < k; ++q)
-                    s = s - W[(size_t)t * m + q] * X[(size_t)q * k + c];
+                    s = fma(-W[(size_t)t * m + q], X[(size_t)q * k + c], s);
                 X[(size_t)t * k + c] = s / W[(size_t)t * m + t];
             }
         for (int t = 0; t < k; ++t) {
             double s = 0.0;
             for (int c = 0; c < k; ++c) {
                 double x = X[(size_t)t * k + c];
-                s = s + x * x;
+                s = fma(x, x, s);
             }
             rho[t] = s;
         }
@@ -420,7 +431,7 @@ int orc_compr(const double *Mt, int r, int m, double tol, double f, int *perm, i
             double s = 0.0;
             for (int i = k; i < r; ++i) {
                 double x = W[(size_t)i * m + k + u];
-                s = s + x * x;
+                s = fma(x, x, s);
             }
             g2[u] = s;
         }
@@ -429,7 +440,7 @@ int orc_compr(const double *Mt, int r, int m, double tol, double f, int *perm, i
         for (int t = 0; t < k; ++t)
             for (int u = 0; u < mk; ++u) {
                 double a = A[(size_t)t * mk + u];
-                double val = a * a + g2[u] * rho[t];
+                double val = fma(a, a, g2[u] * rho[t]);
                 if (val > best) { best = val; bt = t; bu = u; }
             }
         if (best <= f * f) break;

@@ -23,6 +23,7 @@ struct CompressArgs {
     double tol, f, s;
     double lo[3];
     double anchors[kMaxP];
+    double weights[kMaxP];    // w_m = 1 / prod_{n != m} (t_m - t_n)
     int64_t n0, nl;
     const int32_t *leaf;
     const uint64_t *cell;
@@ -116,15 +117,11 @@ __device__ void block_argmax(double v, int64_t idx, Smem<NT> &sh, double &ov, in
     __syncthreads();
 }
 
-// ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n)
-__device__ __forceinline__ double lagrange(int p, const double *anch, int m, double t) {
-    double v = 1.0;
-    for (int n = 0; n < p; ++n) {
-        if (n == m) continue;
-        double num = t - anch[n];
-        double den = anch[m] - anch[n];
-        v = v * (num / den);
-    }
+// ell_m(t) = prod_{n != m} (t - t_n) / (t_m - t_n) = w_m prod_{n != m} (t - t_n)
+__device__ __forceinline__ double lagrange(int p, const double *anch, const double *w, int m, double t) {
+    double v = w[m];
+    for (int n = 0; n < p; ++n)
+        if (n != m) v = v * (t - anch[n]);
     return v;
 }
 
@@ -137,7 +134,7 @@ __device__ void basis_column(const CompressArgs &a, int64_t g, int64_t gid, doub
     for (int ax = 0; ax < a.d; ++ax) {
         double centre = a.lo[ax] + ((double)a.cell[g * 3 + ax] + 0.5) * h;
         double t = (a.pts[gid * 4 + ax] - centre) / half;
-        for (int mm = 0; mm < a.p; ++mm) L[ax][mm] = lagrange(a.p, a.anchors, mm, t);
+        for (int mm = 0; mm < a.p; ++mm) L[ax][mm] = lagrange(a.p, a.anchors, a.weights, mm, t);
     }
     for (int kk = 0; kk < a.r; ++kk) {
         int rem = kk, idx[3] = {0, 0, 0};
@@ -155,7 +152,11 @@ __device__ __forceinline__ int64_t working_gid(const CompressArgs &a, int64_t g,
 // Householder QR of W (r x m, row-major, leading dimension ld).  With pivot:
 // largest remaining column norm (ties: lowest position), stop before step j
 // when |R_jj| <= tol |R_00|; returns the number of steps.  Without pivot:
-// exactly ksteps steps in the current column order.
+// exactly ksteps steps in the current column order.  Sums run over the rows
+// in ascending order with fused multiply-adds; rows are loaded in chunks of
+// kChunk so that several loads of a column are in flight.
+constexpr int kChunk = 8;
+
 template <int NT>
 __device__ int qr_steps(double *W, int ld, int r, int m, Smem<NT> &sh, bool pivot, int ksteps, double tol) {
     const int tid = threadIdx.x;
@@ -163,9 +164,13 @@ __device__ int qr_steps(double *W, int ld, int r, int m, Smem<NT> &sh, bool pivo
     if (pivot) {
         for (int c = tid; c < m; c += NT) {
             double s2 = 0.0;
-            for (int i = 0; i < r; ++i) {
-                double x = W[(int64_t)i * ld + c];
-                s2 = s2 + x * x;
+            for (int i0 = 0; i0 < r; i0 += kChunk) {
+                double x[kChunk];
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) x[u] = i0 + u < r ? W[(int64_t)(i0 + u) * ld + c] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u)
+                    if (i0 + u < r) s2 = __fma_rn(x[u], x[u], s2);
             }
             sh.nrm2[c] = s2;
         }
@@ -207,12 +212,12 @@ __device__ int qr_steps(double *W, int ld, int r, int m, Smem<NT> &sh, bool pivo
             double sigma = 0.0;
             for (int i = j + 1; i < r; ++i) {
                 double x = W[(int64_t)i * ld + j];
-                sigma = sigma + x * x;
+                sigma = __fma_rn(x, x, sigma);
             }
             if (sigma == 0.0) {
                 sh.ctrl[0] = 1.0;  // skip: the column is already reduced
             } else {
-                double nrm = sqrt(alpha * alpha + sigma);
+                double nrm = sqrt(__fma_rn(alpha, alpha, sigma));
                 double beta = alpha <= 0.0 ? nrm : -nrm;
                 sh.ctrl[0] = 0.0;
                 sh.ctrl[1] = (beta - alpha) / beta;  // tau
@@ -231,18 +236,36 @@ __device__ int qr_steps(double *W, int ld, int r, int m, Smem<NT> &sh, bool pivo
             double s2 = 0.0;
             if (!skip) {
                 double w = W[(int64_t)j * ld + c];
-                for (int i = j + 1; i < r; ++i) w = w + sh.v[i] * W[(int64_t)i * ld + c];
+                for (int i0 = j + 1; i0 < r; i0 += kChunk) {
+                    double x[kChunk];
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u) x[u] = i0 + u < r ? W[(int64_t)(i0 + u) * ld + c] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u)
+                        if (i0 + u < r) w = __fma_rn(sh.v[i0 + u], x[u], w);
+                }
                 double tw = tau * w;
                 W[(int64_t)j * ld + c] = W[(int64_t)j * ld + c] - tw;
-                for (int i = j + 1; i < r; ++i) {
-                    double x = W[(int64_t)i * ld + c] - tw * sh.v[i];
-                    W[(int64_t)i * ld + c] = x;
-                    s2 = s2 + x * x;
+                for (int i0 = j + 1; i0 < r; i0 += kChunk) {
+                    double x[kChunk];
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u) x[u] = i0 + u < r ? W[(int64_t)(i0 + u) * ld + c] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u)
+                        if (i0 + u < r) {
+                            double y = __fma_rn(-tw, sh.v[i0 + u], x[u]);
+                            W[(int64_t)(i0 + u) * ld + c] = y;
+                            s2 = __fma_rn(y, y, s2);
+                        }
                 }
             } else {
-                for (int i = j + 1; i < r; ++i) {
-                    double x = W[(int64_t)i * ld + c];
-                    s2 = s2 + x * x;
+                for (int i0 = j + 1; i0 < r; i0 += kChunk) {
+                    double x[kChunk];
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u) x[u] = i0 + u < r ? W[(int64_t)(i0 + u) * ld + c] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < kChunk; ++u)
+                        if (i0 + u < r) s2 = __fma_rn(x[u], x[u], s2);
                 }
             }
             if (pivot) sh.nrm2[c] = s2;
@@ -326,13 +349,13 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
             for (int u = tid; u < mk; u += NT)
                 for (int t = k - 1; t >= 0; --t) {
                     double s = W[(int64_t)t * ld + k + u];
-                    for (int q = t + 1; q < k; ++q) s = s - W[(int64_t)t * ld + q] * W[(int64_t)q * ld + k + u];
+                    for (int q = t + 1; q < k; ++q) s = __fma_rn(-W[(int64_t)t * ld + q], W[(int64_t)q * ld + k + u], s);
                     W[(int64_t)t * ld + k + u] = s / W[(int64_t)t * ld + t];
                 }
             for (int c = tid; c < k; c += NT)
                 for (int t = k - 1; t >= 0; --t) {
                     double s = (t == c) ? 1.0 : 0.0;
-                    for (int q = t + 1; q < k; ++q) s = s - W[(int64_t)t * ld + q] * X[(int64_t)q * k + c];
+                    for (int q = t + 1; q < k; ++q) s = __fma_rn(-W[(int64_t)t * ld + q], X[(int64_t)q * k + c], s);
                     X[(int64_t)t * k + c] = s / W[(int64_t)t * ld + t];
                 }
             __syncthreads();
@@ -340,7 +363,7 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
                 double s = 0.0;
                 for (int c = 0; c < k; ++c) {
                     double x = X[(int64_t)t * k + c];
-                    s = s + x * x;
+                    s = __fma_rn(x, x, s);
                 }
                 sh.rho[t] = s;
             }
@@ -348,7 +371,7 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
                 double s = 0.0;
                 for (int i = k; i < r; ++i) {
                     double x = W[(int64_t)i * ld + k + u];
-                    s = s + x * x;
+                    s = __fma_rn(x, x, s);
                 }
                 sh.nrm2[u] = s;  // gamma_u^2
             }
@@ -359,7 +382,7 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
             for (int64_t e = tid; e < tot; e += NT) {
                 int t = (int)(e / mk), u = (int)(e % mk);
                 double av = W[(int64_t)t * ld + k + u];
-                double val = av * av + sh.nrm2[u] * sh.rho[t];
+                double val = __fma_rn(av, av, sh.nrm2[u] * sh.rho[t]);
                 if (better(val, e, best, bi)) { best = val; bi = e; }
             }
             double bv;
@@ -502,9 +525,15 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
     CK(cudaMemsetAsync(base, 0, 8, st));
 
     // one persistent launch per level, deepest first
-    constexpr int NT = 128;
     double *work = nullptr;
     int64_t work_cap = 0;
+    double weights[kMaxP] = {0};
+    for (int m = 0; m < h->order; ++m) {
+        double den = 1.0;
+        for (int n = 0; n < h->order; ++n)
+            if (n != m) den = den * (h->anchors[m] - h->anchors[n]);
+        weights[m] = 1.0 / den;
+    }
     for (int l = h->L; l >= 2; --l) {
         int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
         int m_cap = (int)std::max<int64_t>(lmax[l], 1);
@@ -512,7 +541,10 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         a.d = h->dim; a.p = h->order; a.r = h->r; a.level = l;
         a.tol = h->tol; a.f = h->f; a.s = h->s;
         for (int i = 0; i < 3; ++i) a.lo[i] = h->lo[i];
-        for (int i = 0; i < kMaxP; ++i) a.anchors[i] = i < h->order ? h->anchors[i] : 0.0;
+        for (int i = 0; i < kMaxP; ++i) {
+            a.anchors[i] = i < h->order ? h->anchors[i] : 0.0;
+            a.weights[i] = i < h->order ? weights[i] : 0.0;
+        }
         a.n0 = n0; a.nl = nl;
         a.leaf = h->leaf; a.cell = h->cell; a.start = start; a.count = cnt;
         a.child0 = h->child0; a.nchild = h->nchild; a.pts = pts; a.skel_gidx = S.skel_gidx;
@@ -521,18 +553,29 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         a.m_cap = m_cap;
         level_setup_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(a);
         LAUNCHED();
+        // threads: one column each where possible
+        const int NT = m_cap <= 64 ? 64 : (m_cap <= 128 ? 128 : 256);
         size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
                            sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
         size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
         a.w_in_smem = (base_smem + w_bytes) <= 160 * 1024;
         size_t smem = base_smem + (a.w_in_smem ? w_bytes : 0);
         a.slot_doubles = (a.w_in_smem ? 0 : (int64_t)h->r * m_cap) + (int64_t)h->r * h->r;
-        auto kern = h->order <= 16 ? compress_kernel<NT, 16> : compress_kernel<NT, kMaxP>;
+        void (*kern)(CompressArgs) = nullptr;
+        bool small_p = h->order <= 16;
+        if (NT == 64) kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
+        else if (NT == 128) kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
+        else kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         if (per_sm < 1) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", smem);
         int64_t grid = std::min<int64_t>(nl, (int64_t)per_sm * h->num_sms);
+        // keep the concurrent node matrices of a global-slot level inside the L2
+        if (!a.w_in_smem) {
+            int64_t fit = (int64_t)(64ll << 20) / (a.slot_doubles * (int64_t)sizeof(double));
+            grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(fit, h->num_sms)));
+        }
         int64_t need = grid * a.slot_doubles;
         if (need > work_cap) {
             if (work) scratch.free(work);
