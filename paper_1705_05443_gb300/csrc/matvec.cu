@@ -137,15 +137,20 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
     const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
     const int ldq = a.ldq;
     const int tid = threadIdx.x;
-    const int per_group = a.tbp * a.nchunks;
+    // targets per thread block row: the smallest power of two >= T (at least
+    // 32, at most a.tbp), the remaining threads split the sources into groups
+    int tbp = 32;
+    while (tbp < T && tbp < a.tbp) tbp *= 2;
+    const int groups = kKsThreads / (tbp * a.nchunks);
+    const int per_group = tbp * a.nchunks;
     const int grp = tid / per_group;
     const int lt = tid % per_group;
-    const int ta = lt % a.tbp;          // target within the block
-    const int ch = lt / a.tbp;          // RHS chunk
-    const bool active = grp < a.groups;
+    const int ta = lt % tbp;          // target within the block
+    const int ch = lt / tbp;            // RHS chunk
+    const bool active = grp < groups;
 
-    for (int tb = 0; tb < T; tb += a.tbp) {
-        const int tcount = min(a.tbp, T - tb);
+    for (int tb = 0; tb < T; tb += tbp) {
+        const int tcount = min(tbp, T - tb);
         const bool have = active && ta < tcount;
         double xa = 0, ya = 0, za = 0;
         if (have) {
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
             }
             __syncthreads();
             if (have) {
-                for (int b = grp; b < fill; b += a.groups) {
+                for (int b = grp; b < fill; b += groups) {
                     P4 y = sy[b];
                     double kv = kappa64<KID>(xa - y.x, ya - y.y, za - y.z);
                     const double *qb = sq + (size_t)b * ldq + ch * RC;
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
             __syncthreads();
         }
         // deterministic reduction over the source groups
-        for (int gg = 0; gg < a.groups; ++gg) {
+        for (int gg = 0; gg < groups; ++gg) {
             if (have && grp == gg) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r) {

@@ -219,15 +219,20 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
     const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
     const int ldq = a.ldq;
     const int tid = threadIdx.x;
-    const int per_group = a.tbp * a.nchunks;
+    // targets per thread block row: the smallest power of two >= T (at least
+    // 32, at most a.tbp), the remaining threads split the sources into groups
+    int tbp = 32;
+    while (tbp < T && tbp < a.tbp) tbp *= 2;
+    const int groups = kDdThreads / (tbp * a.nchunks);
+    const int per_group = tbp * a.nchunks;
     const int grp = tid / per_group;
     const int lt = tid % per_group;
-    const int ta = lt % a.tbp;
-    const int ch = lt / a.tbp;
-    const bool active = grp < a.groups;
+    const int ta = lt % tbp;
+    const int ch = lt / tbp;
+    const bool active = grp < groups;
 
-    for (int tb = 0; tb < T; tb += a.tbp) {
-        const int tcount = min(a.tbp, T - tb);
+    for (int tb = 0; tb < T; tb += tbp) {
+        const int tcount = min(tbp, T - tb);
         const bool have = active && ta < tcount;
         float4 xc[NC];
 #pragma unroll
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
             }
             __syncthreads();
             if (have) {
-                for (int b = grp; b < fill; b += a.groups) {
+                for (int b = grp; b < fill; b += groups) {
                     float dh[3], dl[3];
                     if (EXACT) {
                         float4 yh = sy[b], ym = sy[kDdTile + b], yl = sy[2 * kDdTile + b];
@@ -298,7 +303,7 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
             }
             __syncthreads();
         }
-        for (int gg = 0; gg < a.groups; ++gg) {
+        for (int gg = 0; gg < groups; ++gg) {
             if (have && grp == gg) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r) {
