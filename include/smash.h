@@ -64,10 +64,14 @@ enum {
 /* Arithmetic of the matvec (Section 3.4).  The build is always FP64. */
 enum {
     SMASH_PREC_F64 = 0,   /* FP64 kernel evaluation, transfers and sums */
-    SMASH_PREC_F32X2 = 1  /* coupling and near field in double-float arithmetic on the FP32
+    SMASH_PREC_F32X2 = 1, /* coupling and near field in double-float arithmetic on the FP32
                              pipe (each value hi + lo floats, error-free products and sums,
                              ~1e-12 relative to FP64); transfers FP64.  Kernels 1/|x-y| and
                              1/(x-y) only. */
+    SMASH_PREC_F32 = 2    /* mixed precision: coupling and near field in FP32 (kernel entries,
+                             products, sums; the near field with Kahan-compensated sums),
+                             differences from two-float coordinates; transfers FP64.
+                             ~1e-7..1e-6 relative to FP64.  All kernels. */
 };
 
 typedef struct {

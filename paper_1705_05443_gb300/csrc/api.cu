@@ -234,9 +234,9 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
         build_lists(h, scratch);
         tm.mark();
         build_compression(h, scratch);
-        if (dd_supported(h->kernel_id)) {
-            // double-float copies of the point and skeleton coordinates for the
-            // SMASH_PREC_F32X2 matvec
+        {
+            // normalised two-float copies of the point and skeleton coordinates for
+            // the SMASH_PREC_F32X2 and SMASH_PREC_F32 matvecs
             h->xs_dd = h->mem.alloc<float>((size_t)h->nx * 8);
             dd_coords(h->xs, h->nx, h->lo, h->s, h->xs_dd, h->stream);
             if (h->same) {
@@ -251,6 +251,8 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
                 h->colside.skel_dd = h->mem.alloc<float>((size_t)std::max<int64_t>(h->colside.total_skel, 1) * 8);
                 dd_coords(h->colside.skel_xyz, h->colside.total_skel, h->lo, h->s, h->colside.skel_dd, h->stream);
             }
+        }
+        if (dd_supported(h->kernel_id)) {
             // exact three-float copies: points (near field) and, for deep trees, skeletons
             h->dd_e = dd_exact_exponent(h->s);
             h->xs_x3 = h->mem.alloc<float>((size_t)h->nx * 12);
@@ -294,7 +296,7 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         if (!h) fail(SMASH_EINVAL, "handle is NULL");
         if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
         if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
-        if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2)
+        if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2 && precision != SMASH_PREC_F32)
             fail(SMASH_EINVAL, "unknown precision %d", precision);
         if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
             fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
@@ -312,6 +314,8 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         h->prof_mv.on = profiling_enabled();
         if (precision == SMASH_PREC_F32X2)
             matvec_dd(h, Xd, Yd, nrhs, s, &h->prof_mv);
+        else if (precision == SMASH_PREC_F32)
+            matvec_f32(h, Xd, Yd, nrhs, s, &h->prof_mv);
         else
             matvec_f64(h, Xd, Yd, nrhs, s, &h->prof_mv);
         if (yhost) CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -159,6 +159,8 @@ void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs,
 // matvec with double-float kernel sums (kernels 1/|x-y| and 1/(x-y))
 void matvec_dd(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
 bool dd_supported(int kernel_id);
+// mixed-precision matvec: FP32 kernel sums (Kahan-compensated near field), FP64 transfers
+void matvec_f32(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);

@@ -1,0 +1,280 @@
+// matvec_f32.cu -- the Section 3.4 matvec with the coupling (3.19) and the
+// near field (3.20) in FP32 (SMASH_PREC_F32, the mixed-precision mode).
+//
+//  * Differences come from the normalised two-float coordinates
+//    x'' = 1 + (x - lo)/s in [1, 2): (hi_a - hi_b) is exact (Sterbenz) and
+//    (lo_a - lo_b) restores the low bits, so a difference is accurate to
+//    ~2^-48 in absolute terms before it is rounded to FP32.
+//  * The kernel entry, the products and the sums are FP32 (relative error of
+//    an entry ~1e-7).  The coupling accumulates in FP32; the near field, whose
+//    closest pairs dominate their rows, accumulates with Kahan's compensated
+//    summation.  Sums are written out in FP64; the upward and downward
+//    passes stay FP64.
+//  * Kernels in the normalised frame: 1/|x-y| = (1/s) / |d''|, 1/(x-y) =
+//    (1/s) / d'', log|x-y| = log s + log|d''|, exp(-|x-y|)/|x-y| with
+//    |x-y| = s |d''|.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace smash {
+
+struct KsumF32Args {
+    const int32_t *tnodes;
+    const int64_t *t_off;
+    const int32_t *t_cnt;
+    const int64_t *ptr;
+    const int32_t *col;
+    const int64_t *s_off;
+    const int32_t *s_cnt;
+    const float *xt;   // normalised two-float coordinates, 8 floats per point
+    const float *ys;
+    const float *qv;   // source vectors, FP32, ldq per point
+    double *out;       // target vectors (FP64), ldq
+    double scale;      // multiplies the sums (1/s for 1/r and 1/(x-y), else 1)
+    float s_f;         // s, for the Yukawa kernel
+    float log_s;       // log s, for the log kernel
+    int ldq, nchunks, tbp;
+};
+
+constexpr int kF32Threads = 256;
+constexpr int kF32Tile = 256;
+
+// kernel entry from the FP32 difference d (normalised units)
+template <int KID, int D>
+__device__ __forceinline__ float kappa_f32(const float *d, float s_f, float log_s) {
+    if (KID == SMASH_K_CAUCHY1D) return d[0] != 0.f ? __frcp_rn(d[0]) : 0.f;
+    float r2 = d[0] * d[0];
+    if (D > 1) r2 = fmaf(d[1], d[1], r2);
+    if (D > 2) r2 = fmaf(d[2], d[2], r2);
+    if (r2 == 0.f) return 0.f;
+    if (KID == SMASH_K_INVR) return rsqrtf(r2);
+    if (KID == SMASH_K_LOG) return fmaf(0.5f, __logf(r2), log_s);
+    float ri = rsqrtf(r2);
+    float r = r2 * ri * s_f;
+    return __expf(-r) * (ri / s_f);  // SMASH_K_YUKAWA
+}
+
+template <int KID, int D, int RC, bool KAHAN>
+__global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float4 *syh = reinterpret_cast<float4 *>(smraw);             // kF32Tile
+    float4 *syl = syh + kF32Tile;                                 // kF32Tile
+    float *sq = reinterpret_cast<float *>(syl + kF32Tile);        // kF32Tile * ldq
+    double *red = reinterpret_cast<double *>(sq + (size_t)kF32Tile * a.ldq);  // tbp * ldq
+    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);
+
+    const int64_t g = a.tnodes[blockIdx.x];
+    const int T = a.t_cnt[g];
+    if (T == 0) return;
+    const int64_t toff = a.t_off[g];
+    const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
+    const int ldq = a.ldq;
+    const int tid = threadIdx.x;
+    int tbp = 32;
+    while (tbp < T && tbp < a.tbp) tbp *= 2;
+    const int groups = kF32Threads / (tbp * a.nchunks);
+    const int per_group = tbp * a.nchunks;
+    const int grp = tid / per_group;
+    const int lt = tid % per_group;
+    const int ta = lt % tbp;
+    const int ch = lt / tbp;
+    const bool active = grp < groups;
+
+    for (int tb = 0; tb < T; tb += tbp) {
+        const int tcount = min(tbp, T - tb);
+        const bool have = active && ta < tcount;
+        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
+        if (have) {
+            const float4 *xp = reinterpret_cast<const float4 *>(a.xt + (toff + tb + ta) * 8);
+            xh = xp[0];
+            xl = xp[1];
+        }
+        float acc[RC], cmp[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) { acc[r] = 0.f; cmp[r] = 0.f; }
+        int64_t e = e0;
+        int off = 0;
+        while (e < e1) {
+            int fill = 0;
+            while (e < e1 && fill < kF32Tile) {
+                int j = a.col[e];
+                int S = a.s_cnt[j];
+                int take = min(S - off, kF32Tile - fill);
+                int64_t so = a.s_off[j] + off;
+                for (int q = tid; q < take; q += kF32Threads) sidx[fill + q] = so + q;
+                fill += take;
+                off += take;
+                if (off >= S) { ++e; off = 0; }
+            }
+            __syncthreads();
+            for (int q = tid; q < fill; q += kF32Threads) {
+                const float4 *yp = reinterpret_cast<const float4 *>(a.ys + sidx[q] * 8);
+                syh[q] = yp[0];
+                syl[q] = yp[1];
+            }
+            for (int q = tid; q < fill * ldq; q += kF32Threads) {
+                int b = q / ldq, c = q % ldq;
+                sq[q] = a.qv[sidx[b] * ldq + c];
+            }
+            __syncthreads();
+            if (have) {
+                for (int b = grp; b < fill; b += groups) {
+                    float4 yh = syh[b], yl = syl[b];
+                    float d[3] = {(xh.x - yh.x) + (xl.x - yl.x), (xh.y - yh.y) + (xl.y - yl.y),
+                                  (xh.z - yh.z) + (xl.z - yl.z)};
+                    float kv = kappa_f32<KID, D>(d, a.s_f, a.log_s);
+                    const float *qb = sq + (size_t)b * ldq + ch * RC;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        if (KAHAN) {
+                            float y = fmaf(kv, qb[r], -cmp[r]);
+                            float t = acc[r] + y;
+                            cmp[r] = (t - acc[r]) - y;
+                            acc[r] = t;
+                        } else {
+                            acc[r] = fmaf(kv, qb[r], acc[r]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        for (int gg = 0; gg < groups; ++gg) {
+            if (have && grp == gg) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    double v = KAHAN ? (double)acc[r] - (double)cmp[r] : (double)acc[r];
+                    double *dst = red + (size_t)ta * ldq + ch * RC + r;
+                    *dst = gg == 0 ? v : *dst + v;
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < tcount * ldq; q += kF32Threads) a.out[(toff + tb) * ldq + q] = red[q] * a.scale;
+        __syncthreads();
+    }
+}
+
+template <int KID, int D, bool KAHAN>
+static void launch_f32(KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
+    if (ntn <= 0) return;
+    size_t smem = sizeof(float4) * 2 * kF32Tile + sizeof(float) * (size_t)kF32Tile * a.ldq +
+                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * kF32Tile;
+    void (*kern)(KsumF32Args) = nullptr;
+    switch (RC) {
+    case 1: kern = ksum_f32_kernel<KID, D, 1, KAHAN>; break;
+    case 2: kern = ksum_f32_kernel<KID, D, 2, KAHAN>; break;
+    case 4: kern = ksum_f32_kernel<KID, D, 4, KAHAN>; break;
+    case 8: kern = ksum_f32_kernel<KID, D, 8, KAHAN>; break;
+    case 16: kern = ksum_f32_kernel<KID, D, 16, KAHAN>; break;
+    default: kern = ksum_f32_kernel<KID, D, 32, KAHAN>; break;
+    }
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)ntn, kF32Threads, smem, s>>>(a);
+    LAUNCHED();
+}
+
+template <bool KAHAN>
+static void dispatch_f32(int kid, int dim, KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
+    switch (kid) {
+    case SMASH_K_CAUCHY1D: launch_f32<SMASH_K_CAUCHY1D, 1, KAHAN>(a, ntn, RC, s); return;
+    case SMASH_K_LOG:
+        if (dim == 3) launch_f32<SMASH_K_LOG, 3, KAHAN>(a, ntn, RC, s);
+        else if (dim == 2) launch_f32<SMASH_K_LOG, 2, KAHAN>(a, ntn, RC, s);
+        else launch_f32<SMASH_K_LOG, 1, KAHAN>(a, ntn, RC, s);
+        return;
+    case SMASH_K_INVR:
+        if (dim == 3) launch_f32<SMASH_K_INVR, 3, KAHAN>(a, ntn, RC, s);
+        else if (dim == 2) launch_f32<SMASH_K_INVR, 2, KAHAN>(a, ntn, RC, s);
+        else launch_f32<SMASH_K_INVR, 1, KAHAN>(a, ntn, RC, s);
+        return;
+    default:
+        if (dim == 3) launch_f32<SMASH_K_YUKAWA, 3, KAHAN>(a, ntn, RC, s);
+        else if (dim == 2) launch_f32<SMASH_K_YUKAWA, 2, KAHAN>(a, ntn, RC, s);
+        else launch_f32<SMASH_K_YUKAWA, 1, KAHAN>(a, ntn, RC, s);
+        return;
+    }
+}
+
+static void ksum_f32(const smash_h2 *h, bool kahan, KsumF32Args a, int64_t ntn, int max_targets, int RC,
+                     cudaStream_t s) {
+    a.nchunks = a.ldq / RC;
+    int tbp = 32;
+    while (tbp < max_targets && tbp * 2 * a.nchunks <= kF32Threads) tbp *= 2;
+    if (tbp * a.nchunks > kF32Threads) tbp = std::max(1, kF32Threads / a.nchunks);
+    a.tbp = tbp;
+    const bool mult = h->kernel_id == SMASH_K_INVR || h->kernel_id == SMASH_K_CAUCHY1D;
+    a.scale = mult ? 1.0 / h->s : 1.0;
+    a.s_f = (float)h->s;
+    a.log_s = (float)log(h->s);
+    if (kahan)
+        dispatch_f32<true>(h->kernel_id, h->dim, a, ntn, RC, s);
+    else
+        dispatch_f32<false>(h->kernel_id, h->dim, a, ntn, RC, s);
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ in, int64_t n, float *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __double2float_rn(in[i]);
+}
+
+static void to_f32(const double *in, int64_t n, float *out, cudaStream_t s) {
+    if (n <= 0) return;
+    to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, out);
+    LAUNCHED();
+}
+
+void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof) {
+    const Side &R = h->row;
+    const Side &Cs = *h->col;
+    int ldq, RC;
+    if (nrhs <= 32) {
+        RC = 1;
+        while (RC < nrhs) RC *= 2;
+        ldq = RC;
+    } else {
+        RC = 32;
+        ldq = (nrhs + 31) / 32 * 32;
+    }
+    Arena tmp(s);
+    double *qs = tmp.alloc<double>((size_t)h->ny * ldq);
+    double *zs = tmp.alloc<double>((size_t)h->nx * ldq);
+    double *qhat = tmp.alloc<double>((size_t)std::max<int64_t>(Cs.total_skel, 1) * ldq);
+    double *zhat = tmp.alloc<double>((size_t)std::max<int64_t>(R.total_skel, 1) * ldq);
+    float *qs1 = tmp.alloc<float>((size_t)h->ny * ldq);
+    float *qhat1 = tmp.alloc<float>((size_t)std::max<int64_t>(Cs.total_skel, 1) * ldq);
+    PhaseTimer tm(s, prof);
+    tm.mark();
+    matvec_gather(h, X, nrhs, ldq, qs, s);
+    to_f32(qs, h->ny * ldq, qs1, s);
+    tm.mark();
+    {
+        KsumF32Args a{};
+        a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
+        a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
+        a.xt = h->xs_dd; a.ys = h->ys_dd; a.qv = qs1; a.out = zs; a.ldq = ldq;
+        ksum_f32(h, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+    }
+    tm.mark();
+    matvec_upward(h, qs, qhat, ldq, s);
+    to_f32(qhat, Cs.total_skel * ldq, qhat1, s);
+    tm.mark();
+    if (h->nnodes > 1) {
+        KsumF32Args a{};
+        a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
+        a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
+        a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.qv = qhat1; a.out = zhat; a.ldq = ldq;
+        ksum_f32(h, false, a, h->nnodes - 1, h->r, RC, s);
+    }
+    tm.mark();
+    matvec_downward(h, zhat, zs, ldq, s);
+    tm.mark();
+    matvec_scatter(h, zs, ldq, nrhs, Y, s);
+    tm.mark();
+    tm.finish(4);
+    tmp.release();
+}
+
+}  // namespace smash
