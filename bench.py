@@ -120,6 +120,80 @@ def run_cpu_oracle(n: int, w: dict) -> dict:
     return {"value": n / dt, "seconds": dt}
 
 
+def run_serving(sm, torch, requests: int, rate: float, seed: int, precision: int, max_inflight: int = 4) -> dict:
+    """Poisson stream of construct-and-apply requests shaped like the serving
+    configuration (1D Cauchy-like kernel 1/(x_i - y_j), x ~ U[0,1],
+    y = x + 1e-3 U, N log-uniform in [2^12, 2^20], leaf 64, order 16,
+    tol 1e-10, 1..64 right-hand sides), served by the library's request
+    server and, for comparison, one request at a time by the plain path with
+    the same arrival times.  Inputs are prefixes of pinned host pools."""
+    g = np.random.default_rng(seed)
+    nmax = 1 << 20
+    xp = torch.from_numpy(g.random((nmax, 1))).pin_memory()
+    yp = (xp + 1e-3 * torch.from_numpy(g.random((nmax, 1)))).pin_memory()
+    Xp = torch.from_numpy(g.standard_normal(nmax * 64)).pin_memory()
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=requests))
+    sizes = np.floor(2.0 ** g.uniform(12, 20, size=requests)).astype(int)
+    nrhs = g.integers(1, 65, size=requests)
+    Ys = [torch.empty((int(n), int(k)), dtype=torch.float64).pin_memory() for n, k in zip(sizes, nrhs)]
+    Xs = [Xp[: int(n) * int(k)].view(int(n), int(k)) for n, k in zip(sizes, nrhs)]
+    leaf, order, tol, kid = 64, 16, 1e-10, sm.SMASH_K_CAUCHY1D
+
+    # warm the kernels and the pools once
+    srv = sm.SmashServer(max_inflight=max_inflight, precision=precision)
+    srv.wait(srv.submit(xp[:4096], kid, leaf, order, tol, Xs[0][:0].new_empty((4096, 1)).fill_(1.0),
+                        y=yp[:4096]))
+
+    lat, done_at = [None] * requests, [None] * requests
+    t0 = time.perf_counter()
+    tickets = [None] * requests
+
+    def waiter():
+        for i in range(requests):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            _, st = srv.wait(tickets[i])
+            done_at[i] = time.perf_counter() - t0
+            lat[i] = st["latency_ms"]
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    for i in range(requests):
+        dt = arrivals[i] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        n = int(sizes[i])
+        tickets[i] = srv.submit(xp[:n], kid, leaf, order, tol, Xs[i], y=yp[:n], Y=Ys[i])
+    th.join()
+    makespan = max(done_at)
+    seen = srv.max_inflight_seen()
+    srv.close()
+
+    # one request at a time, same arrival times
+    plain_lat = []
+    t0 = time.perf_counter()
+    for i in range(requests):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        n = int(sizes[i])
+        h = sm.smash_build_xy(xp[:n], yp[:n], kid, leaf, order, tol)
+        sm.smash_matvec_ex(h, Xs[i], Ys[i], precision)
+        sm.smash_free(h)
+        plain_lat.append((time.perf_counter() - t0 - arrivals[i]) * 1e3)
+    plain_makespan = time.perf_counter() - t0
+    pts = float(sizes.sum())
+    return {
+        "workload": f"{requests} requests, Poisson {rate:.0f}/s, 1D Cauchy-like, N log-uniform 2^12..2^20, "
+                    "leaf 64, order 16, tol 1e-10, 1-64 RHS",
+        "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "points_per_s": pts / makespan, "max_inflight": max_inflight, "max_inflight_seen": seen},
+        "plain_one_at_a_time": {"p50_ms": float(np.percentile(plain_lat, 50)),
+                                "p99_ms": float(np.percentile(plain_lat, 99)),
+                                "points_per_s": pts / plain_makespan},
+    }
+
+
 def bench_reference(args, w):
     ws, rank = _dist()
     if rank != 0:
@@ -288,6 +362,9 @@ def bench_ours(args, w):
         wdef = (f"per kernel entry {DD_MAC_OPS}*nrhs + {DD_EVAL_OPS} FP32 instructions of the "
                 "double-float algorithm (error-free products and sums)")
     achieved = cpl_work / (cpl_ms / 1e3) / 1e12
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(sm, torch, args.serve_requests, 200.0, 4000, prec)
     cpu = run_cpu_oracle(CPU_SAMPLE_N, w) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -312,6 +389,7 @@ def bench_ours(args, w):
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(x_np.nbytes + q_np.nbytes), "d2h_bytes_per_step": int(q_np.nbytes)},
         "gpu_launches": int(launches / args.steps),
+        "serving": serving,
         "clocks": clocks,
         "wall_s": wall,
         "peaks_file": peak_src,
@@ -334,6 +412,8 @@ def main():
     ap.add_argument("--workload", default="3d_invr_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe); for profiling cases")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving measurement (0 = skip)")
     ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64"],
                     help="matvec arithmetic: double-float kernel sums (FP64-accurate) or plain FP64")
     args = ap.parse_args()

@@ -164,6 +164,55 @@ SMASH_API smash_status smash_matvec_noalloc(smash_handle h, const double *X, dou
  * handle's pending work first. */
 SMASH_API void smash_free(smash_handle h);
 
+/*
+ * Request server (host runtime around smash_build_xy and smash_matvec_ex).
+ * Construct-and-apply requests are admitted in arrival order as in-flight
+ * slots and device memory allow: a request starts when fewer than
+ * max_inflight requests run and its predicted footprint
+ * (smash_predict_footprint plus its vectors) fits the unreserved budget; a
+ * request that does not fit runs alone once nothing else is in flight.  Each
+ * of the max_inflight worker threads owns a CUDA stream, so admitted requests
+ * build and apply concurrently and their kernels overlap on the device.  A
+ * request may keep its representation resident (counted against the budget
+ * until released) and later apply requests reuse it.  Buffers are not
+ * copied: points, X and Y (host or device memory) must stay valid until
+ * smash_server_wait has returned for the request; Y is complete then.  The
+ * paper has no counterpart (deployment runtime).
+ */
+typedef struct smash_server *smash_server_t;
+
+typedef struct {
+    double queue_ms;        /* submission to admission */
+    double service_ms;      /* admission to completion */
+    double latency_ms;      /* submission to completion */
+    size_t predicted_bytes; /* admission estimate */
+    int64_t resident_id;    /* id of the kept representation (0 if none) */
+    int64_t points;         /* nx of a construct request, 0 for apply */
+} smash_request_stats;
+
+/* mem_budget_bytes == 0: 80 % of the free device memory at creation.
+ * precision: SMASH_PREC_* of the served matvecs.  Errors: SMASH_EINVAL, SMASH_ECUDA. */
+SMASH_API smash_status smash_server_create(int max_inflight, size_t mem_budget_bytes, int precision,
+                                           smash_server_t *out);
+/* Queues build(x[, y]) + Y = A^ X; arguments as smash_build_xy / smash_matvec.
+ * keep != 0 keeps the representation resident. */
+SMASH_API smash_status smash_server_submit(smash_server_t s, const double *x, int64_t nx, const double *y,
+                                           int64_t ny, int dim, int kernel_id, int leaf_size, int order,
+                                           double tol, const double *X, int nrhs, double *Y, int keep,
+                                           int64_t *ticket);
+/* Queues Y = A^ X on a resident representation (X: ny x nrhs, Y: nx x nrhs). */
+SMASH_API smash_status smash_server_apply(smash_server_t s, int64_t resident_id, const double *X, int nrhs,
+                                          double *Y, int64_t *ticket);
+/* Blocks until the request completes and fills *stats (may be NULL).
+ * Returns the request's status. */
+SMASH_API smash_status smash_server_wait(smash_server_t s, int64_t ticket, smash_request_stats *stats);
+/* Frees a resident representation. */
+SMASH_API smash_status smash_server_release(smash_server_t s, int64_t resident_id);
+/* Largest number of requests that were in flight at the same time. */
+SMASH_API int smash_server_max_inflight_seen(smash_server_t s);
+/* Finishes the queued requests, joins the workers, frees resident representations. */
+SMASH_API void smash_server_destroy(smash_server_t s);
+
 /* Sizes and statistics of a built representation. */
 typedef struct {
     int64_t nx, ny;

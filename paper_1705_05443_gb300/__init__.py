@@ -24,7 +24,7 @@ __all__ = [
     "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
-    "smash_last_profile", "H2Matrix", "load_library", "library_path",
+    "smash_last_profile", "H2Matrix", "SmashServer", "load_library", "library_path",
     "SMASH_K_LOG", "SMASH_K_INVR", "SMASH_K_YUKAWA", "SMASH_K_CAUCHY1D", "SMASH_PREC_F64", "SMASH_PREC_F32X2", "SMASH_PREC_F32",
     "PROFILE_PHASES",
 ]
@@ -121,6 +121,21 @@ def load_library(build: bool = True):
     lib.smash_set_profiling.restype = None
     lib.smash_last_profile.argtypes = [P, P, i32]
     lib.smash_last_profile.restype = i32
+    lib.smash_server_create.argtypes = [i32, C.c_size_t, i32, C.POINTER(P)]
+    lib.smash_server_create.restype = i32
+    lib.smash_server_submit.argtypes = [P, P, i64, P, i64, i32, i32, i32, i32, dbl, P, i32, P, i32,
+                                        C.POINTER(i64)]
+    lib.smash_server_submit.restype = i32
+    lib.smash_server_apply.argtypes = [P, i64, P, i32, P, C.POINTER(i64)]
+    lib.smash_server_apply.restype = i32
+    lib.smash_server_wait.argtypes = [P, i64, P]
+    lib.smash_server_wait.restype = i32
+    lib.smash_server_release.argtypes = [P, i64]
+    lib.smash_server_release.restype = i32
+    lib.smash_server_max_inflight_seen.argtypes = [P]
+    lib.smash_server_max_inflight_seen.restype = i32
+    lib.smash_server_destroy.argtypes = [P]
+    lib.smash_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -277,6 +292,77 @@ def smash_last_profile(h) -> dict:
     ms = np.zeros(len(PROFILE_PHASES))
     n = load_library().smash_last_profile(h, C.c_void_p(ms.ctypes.data), len(ms))
     return dict(zip(PROFILE_PHASES[:n], ms[:n].tolist()))
+
+
+class smash_request_stats(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("service_ms", C.c_double), ("latency_ms", C.c_double),
+                ("predicted_bytes", C.c_size_t), ("resident_id", C.c_int64), ("points", C.c_int64)]
+
+
+class SmashServer:
+    """The library's request server (smash_server_*): construct-and-apply
+    requests admitted by in-flight slots and device-memory budget, run by
+    worker threads on their own streams.  Buffers (numpy or torch, host or
+    device) are not copied: this wrapper keeps references to them until the
+    request has been waited on."""
+
+    def __init__(self, max_inflight: int = 4, mem_budget_bytes: int = 0, precision: int = SMASH_PREC_F64):
+        lib = load_library()
+        self._s = C.c_void_p()
+        _check(lib.smash_server_create(max_inflight, mem_budget_bytes, precision, C.byref(self._s)))
+        self._live = {}
+
+    def submit(self, x, kernel_id: int, leaf_size: int, order: int, tol: float, X, y=None, keep: bool = False,
+               Y=None) -> int:
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            y = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
+        if Y is None:
+            Y = X.new_empty((x.shape[0], X.shape[1])) if hasattr(X, "new_empty") else np.empty((x.shape[0], X.shape[1]))
+        t = C.c_int64()
+        _check(load_library().smash_server_submit(
+            self._s, _ptr(x), int(x.shape[0]), _ptr(y), 0 if y is None else int(y.shape[0]), int(x.shape[1]),
+            kernel_id, leaf_size, order, float(tol), _ptr(X), int(X.shape[1]), _ptr(Y), 1 if keep else 0,
+            C.byref(t)))
+        self._live[t.value] = (x, y, X, Y)
+        return t.value
+
+    def apply(self, resident_id: int, X, nx: int, Y=None) -> int:
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float64)
+        if Y is None:
+            Y = X.new_empty((nx, X.shape[1])) if hasattr(X, "new_empty") else np.empty((nx, X.shape[1]))
+        t = C.c_int64()
+        _check(load_library().smash_server_apply(self._s, resident_id, _ptr(X), int(X.shape[1]), _ptr(Y),
+                                                 C.byref(t)))
+        self._live[t.value] = (None, None, X, Y)
+        return t.value
+
+    def wait(self, ticket: int):
+        """(Y, stats dict) of a finished request; raises SmashError on failure."""
+        st = smash_request_stats()
+        code = load_library().smash_server_wait(self._s, ticket, C.byref(st))
+        bufs = self._live.pop(ticket, None)
+        _check(code)
+        return bufs[3], {name: getattr(st, name) for name, _ in smash_request_stats._fields_}
+
+    def release(self, resident_id: int):
+        _check(load_library().smash_server_release(self._s, resident_id))
+
+    def max_inflight_seen(self) -> int:
+        return int(load_library().smash_server_max_inflight_seen(self._s))
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and self._s.value:
+            load_library().smash_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class H2Matrix:

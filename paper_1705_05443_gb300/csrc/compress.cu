@@ -566,7 +566,7 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         if (NT == 64) kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
         else if (NT == 128) kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
         else kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
-        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_dynamic_smem((const void *)kern);
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         if (per_sm < 1) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", smem);

@@ -180,6 +180,11 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X_dev, double *Y_dev, i
 
 bool profiling_enabled();
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per kernel.  The limit is a per-function setting shared by all
+// host threads, so it is only ever raised, never set per launch.
+void allow_max_dynamic_smem(const void *func);
+
 // Message returned by smash_last_error() on this host thread.
 void set_last_error(const char *msg);
 

@@ -224,7 +224,7 @@ static void launch_ksum(KsumArgs a, int64_t ntn, int RC, cudaStream_t s) {
     case 16: kern = ksum_f64_kernel<KID, 16>; break;
     default: kern = ksum_f64_kernel<KID, 32>; break;
     }
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void *)kern);
     kern<<<(unsigned)ntn, kKsThreads, smem, s>>>(a);
     LAUNCHED();
 }

@@ -334,7 +334,7 @@ static void launch_dd(KsumDDArgs a, int64_t ntn, int RC, cudaStream_t s) {
     case 16: kern = ksum_dd_kernel<KID, D, 16, EXACT>; break;
     default: kern = ksum_dd_kernel<KID, D, 32, EXACT>; break;
     }
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void *)kern);
     kern<<<(unsigned)ntn, kDdThreads, smem, s>>>(a);
     LAUNCHED();
 }

@@ -171,7 +171,7 @@ static void launch_f32(KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
     case 16: kern = ksum_f32_kernel<KID, D, 16, KAHAN>; break;
     default: kern = ksum_f32_kernel<KID, D, 32, KAHAN>; break;
     }
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void *)kern);
     kern<<<(unsigned)ntn, kF32Threads, smem, s>>>(a);
     LAUNCHED();
 }

@@ -1,6 +1,7 @@
 // util.cu -- errors, stream-ordered arena, device scan, LSD radix sort.
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -57,6 +58,20 @@ void Arena::release() {
     for (auto &b : blocks_) cudaFreeAsync(b.p, stream_);
     blocks_.clear();
     bytes_ = 0;
+}
+
+// ---------------------------------------------------------------- kernel attributes
+void allow_max_dynamic_smem(const void *func) {
+    static std::mutex mu;
+    static std::vector<const void *> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const void *f : done)
+        if (f == func) return;
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    done.push_back(func);
 }
 
 // ---------------------------------------------------------------- timing
