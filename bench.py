@@ -40,6 +40,7 @@ NUM_SMS = 152
 PAIR_EVAL_FLOPS = 9        # FP64: squared distance (8) + reciprocal square root (1) per kernel entry
 DD_EVAL_OPS = 54           # double-float: FP32 instructions of one 1/|x-y| entry (difference, square, rsqrt + Newton)
 DD_MAC_OPS = 12            # double-float: FP32 instructions of one error-free multiply-accumulate
+F32_EVAL_OPS = 14          # FP32: two-float difference (9), squared distance (3), rsqrt + select (2)
 
 
 def _dist():
@@ -235,9 +236,8 @@ def bench_ours(args, w):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     sm.load_library()
     n = w["n"]
-    seed = w["index"] * 1000 + rank
-    x_np = si.uniform_cube(n, w["d"], seed)
-    q_np = si.rhs(n, w["nrhs"], seed + 500)
+    wl = si.make_workload(args.workload, rep=rank, n=n)
+    x_np, q_np = wl["x"], wl["q"]
     x = torch.from_numpy(x_np).to(dev)
     q = torch.from_numpy(q_np).to(dev)
     z = torch.empty_like(q)
@@ -248,7 +248,7 @@ def bench_ours(args, w):
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
 
-    prec = sm.SMASH_PREC_F32X2 if args.precision == "f32x2" else sm.SMASH_PREC_F64
+    prec = {"f32x2": sm.SMASH_PREC_F32X2, "f64": sm.SMASH_PREC_F64, "f32": sm.SMASH_PREC_F32}[args.precision]
 
     def step(host=False, precision=prec):
         if host:
@@ -353,6 +353,13 @@ def bench_ours(args, w):
         psrc = (f"FP64 {FP64_FLOPS_PER_CLK_SM} flop/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
                 "(nominal unit count, sampled clock; an FMA probe measured 1.19 TFLOP/s)")
         wdef = f"per kernel entry 2*nrhs + {PAIR_EVAL_FLOPS} FP64 flops"
+    elif prec == sm.SMASH_PREC_F32:
+        peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        cpl_work = info["coupling_pairs"] * (nrhs + F32_EVAL_OPS)
+        kname = "coupling (ksum_f32_kernel over L)"
+        psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                "(one FMA = one operation)")
+        wdef = f"per kernel entry nrhs FMAs + {F32_EVAL_OPS} FP32 instructions (difference, distance, kernel)"
     else:
         peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         cpl_work = info["coupling_pairs"] * (DD_MAC_OPS * nrhs + DD_EVAL_OPS)
@@ -369,13 +376,17 @@ def bench_ours(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if prec != sm.SMASH_PREC_F64 else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {sm.SMASH_PREC_F32X2: "f32x2", sm.SMASH_PREC_F64: "f64", sm.SMASH_PREC_F32: "f32"}[prec],
         "data": "synthetic",
-        "config": {"workload": "3d_invr uniform cube N=2^20" if n == 1 << 20 else f"3d_invr uniform cube N={n}",
-                   "n": n, "dim": 3, "kernel": "1/|x-y|",
+        "config": {"workload": (args.workload if args.workload != "3d_invr_1m" else "3d_invr uniform cube N=2^20")
+                   + ("" if n == 1 << 20 else f" at N={n}"),
+                   "n": n, "dim": w["d"], "kernel": {0: "log|x-y|", 1: "1/|x-y|", 2: "exp(-|x-y|)/|x-y|",
+                                                     3: "1/(x-y)"}[w["kernel"]],
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
-                   "precision": "build fp64; matvec " + ("fp64" if prec == sm.SMASH_PREC_F64 else
-                                                          "double-float kernel sums, fp64 transfers"),
+                   "precision": "build fp64; matvec " + {sm.SMASH_PREC_F64: "fp64",
+                                                          sm.SMASH_PREC_F32X2: "double-float kernel sums, fp64 transfers",
+                                                          sm.SMASH_PREC_F32: "fp32 kernel sums, fp64 transfers"}[prec],
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -414,8 +425,9 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe); for profiling cases")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0 = skip)")
-    ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64"],
-                    help="matvec arithmetic: double-float kernel sums (FP64-accurate) or plain FP64")
+    ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64", "f32"],
+                    help="matvec arithmetic: double-float kernel sums (FP64-accurate), plain FP64, or "
+                         "mixed precision FP32")
     args = ap.parse_args()
     w = dict(si.WORKLOADS[args.workload])
     if args.n:

@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "ksum_tiles.cuh"
 
 namespace smash {
 
@@ -125,6 +126,7 @@ constexpr int kKsTile = 128;  // source points staged per round
 template <int KID, int RC>
 __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ PartnerChunk pc;
     P4 *sy = reinterpret_cast<P4 *>(smraw);                     // kKsTile
     double *sq = reinterpret_cast<double *>(sy + kKsTile);                // kKsTile * ldq
     double *red = sq + (size_t)kKsTile * a.ldq;                          // tbp * ldq
@@ -161,21 +163,13 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
 #pragma unroll
         for (int r = 0; r < RC; ++r) acc[r] = 0.0;
         // walk the source stream: partners e0..e1, each a run of points
-        int64_t e = e0;
-        int off = 0;
-        while (e < e1) {
-            // fill the tile with the next (up to) kKsTile source points
-            int fill = 0;
-            while (e < e1 && fill < kKsTile) {
-                int j = a.col[e];
-                int S = a.s_cnt[j];
-                int take = min(S - off, kKsTile - fill);
-                int64_t so = a.s_off[j] + off;
-                for (int q = tid; q < take; q += kKsThreads) sidx[fill + q] = so + q;
-                fill += take;
-                off += take;
-                if (off >= S) { ++e; off = 0; }
-            }
+        for (int64_t e = e0; e < e1;) {
+            load_partner_chunk<kKsThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+            const int nchunk = pc.n, total = pc.pre[pc.n];
+            e += nchunk;
+            for (int pos = 0; pos < total; pos += kKsTile) {
+            const int fill = min(kKsTile, total - pos);
+            for (int q = tid; q < fill; q += kKsThreads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill; q += kKsThreads) sy[q] = reinterpret_cast<const P4 *>(a.ys)[sidx[q]];
             for (int q = tid; q < fill * ldq; q += kKsThreads) {
@@ -188,11 +182,20 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
                     P4 y = sy[b];
                     double kv = kappa64<KID>(xa - y.x, ya - y.y, za - y.z);
                     const double *qb = sq + (size_t)b * ldq + ch * RC;
+                    if (RC >= 2) {
 #pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] += kv * qb[r];
+                        for (int r = 0; r < RC; r += 2) {
+                            double2 v = *reinterpret_cast<const double2 *>(qb + r);
+                            acc[r] += kv * v.x;
+                            acc[r + 1] += kv * v.y;
+                        }
+                    } else {
+                        acc[0] += kv * qb[0];
+                    }
                 }
             }
             __syncthreads();
+            }
         }
         // deterministic reduction over the source groups
         for (int gg = 0; gg < groups; ++gg) {

@@ -35,6 +35,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "ksum_tiles.cuh"
 
 namespace smash {
 
@@ -206,6 +207,7 @@ constexpr int kDdTile = 128;
 template <int KID, int D, int RC, bool EXACT>
 __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ PartnerChunk pc;
     constexpr int NC = EXACT ? 3 : 2;                                 // float4 per point
     float4 *sy = reinterpret_cast<float4 *>(smraw);                  // kDdTile * NC
     float2 *sq = reinterpret_cast<float2 *>(sy + NC * kDdTile);      // kDdTile * ldq
@@ -245,20 +247,13 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
         float ah[RC], al[RC];
 #pragma unroll
         for (int r = 0; r < RC; ++r) { ah[r] = 0.f; al[r] = 0.f; }
-        int64_t e = e0;
-        int off = 0;
-        while (e < e1) {
-            int fill = 0;
-            while (e < e1 && fill < kDdTile) {
-                int j = a.col[e];
-                int S = a.s_cnt[j];
-                int take = min(S - off, kDdTile - fill);
-                int64_t so = a.s_off[j] + off;
-                for (int q = tid; q < take; q += kDdThreads) sidx[fill + q] = so + q;
-                fill += take;
-                off += take;
-                if (off >= S) { ++e; off = 0; }
-            }
+        for (int64_t e = e0; e < e1;) {
+            load_partner_chunk<kDdThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+            const int nchunk = pc.n, total = pc.pre[pc.n];
+            e += nchunk;
+            for (int pos = 0; pos < total; pos += kDdTile) {
+            const int fill = min(kDdTile, total - pos);
+            for (int q = tid; q < fill; q += kDdThreads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill * NC; q += kDdThreads) {
                 int b = q / NC, c = q % NC;
@@ -285,9 +280,20 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
                     float kh, kl;
                     kappa_dd<KID, D>(dh, dl, kh, kl);
                     const float2 *qb = sq + (size_t)b * ldq + ch * RC;
+                    float2 qv[RC];
+                    if (RC >= 2) {
+#pragma unroll
+                        for (int r = 0; r < RC; r += 2) {
+                            float4 v = *reinterpret_cast<const float4 *>(qb + r);
+                            qv[r] = make_float2(v.x, v.y);
+                            qv[r + 1] = make_float2(v.z, v.w);
+                        }
+                    } else {
+                        qv[0] = qb[0];
+                    }
 #pragma unroll
                     for (int r = 0; r < RC; ++r) {
-                        float2 qq = qb[r];
+                        float2 qq = qv[r];
                         float p = kh * qq.x;
                         float pe = fmaf(kh, qq.x, -p);
                         pe = fmaf(kh, qq.y, pe);
@@ -302,6 +308,7 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
                 for (int r = 0; r < RC; ++r) fast_two_sum(ah[r], al[r], ah[r], al[r]);
             }
             __syncthreads();
+            }
         }
         for (int gg = 0; gg < groups; ++gg) {
             if (have && grp == gg) {

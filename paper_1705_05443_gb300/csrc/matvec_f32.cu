@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "ksum_tiles.cuh"
 
 namespace smash {
 
@@ -56,14 +57,18 @@ __device__ __forceinline__ float kappa_f32(const float *d, float s_f, float log_
     return __expf(-r) * (ri / s_f);  // SMASH_K_YUKAWA
 }
 
-template <int KID, int D, int RC, bool KAHAN>
+// One thread: TA targets x RC right-hand sides; the right-hand sides of a
+// source are read from shared memory as float4 (RC >= 4) and reused by the
+// TA targets.
+template <int KID, int D, int RC, bool KAHAN, int TA>
 __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ PartnerChunk pc;
     float4 *syh = reinterpret_cast<float4 *>(smraw);             // kF32Tile
     float4 *syl = syh + kF32Tile;                                 // kF32Tile
     float *sq = reinterpret_cast<float *>(syl + kF32Tile);        // kF32Tile * ldq
-    double *red = reinterpret_cast<double *>(sq + (size_t)kF32Tile * a.ldq);  // tbp * ldq
-    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);
+    double *red = reinterpret_cast<double *>(sq + (size_t)kF32Tile * a.ldq);  // TA * tbp * ldq
+    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)TA * a.tbp * a.ldq);
 
     const int64_t g = a.tnodes[blockIdx.x];
     const int T = a.t_cnt[g];
@@ -72,8 +77,8 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
     const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
     const int ldq = a.ldq;
     const int tid = threadIdx.x;
-    int tbp = 32;
-    while (tbp < T && tbp < a.tbp) tbp *= 2;
+    int tbp = 32;  // thread rows; each covers TA targets
+    while (tbp * TA < T && tbp < a.tbp) tbp *= 2;
     const int groups = kF32Threads / (tbp * a.nchunks);
     const int per_group = tbp * a.nchunks;
     const int grp = tid / per_group;
@@ -81,33 +86,36 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
     const int ta = lt % tbp;
     const int ch = lt / tbp;
     const bool active = grp < groups;
+    const int span = TA * tbp;
 
-    for (int tb = 0; tb < T; tb += tbp) {
-        const int tcount = min(tbp, T - tb);
-        const bool have = active && ta < tcount;
-        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
-        if (have) {
-            const float4 *xp = reinterpret_cast<const float4 *>(a.xt + (toff + tb + ta) * 8);
-            xh = xp[0];
-            xl = xp[1];
-        }
-        float acc[RC], cmp[RC];
+    for (int tb = 0; tb < T; tb += span) {
+        const int tcount = min(span, T - tb);
+        bool have[TA];
+        float4 xh[TA], xl[TA];
 #pragma unroll
-        for (int r = 0; r < RC; ++r) { acc[r] = 0.f; cmp[r] = 0.f; }
-        int64_t e = e0;
-        int off = 0;
-        while (e < e1) {
-            int fill = 0;
-            while (e < e1 && fill < kF32Tile) {
-                int j = a.col[e];
-                int S = a.s_cnt[j];
-                int take = min(S - off, kF32Tile - fill);
-                int64_t so = a.s_off[j] + off;
-                for (int q = tid; q < take; q += kF32Threads) sidx[fill + q] = so + q;
-                fill += take;
-                off += take;
-                if (off >= S) { ++e; off = 0; }
+        for (int u = 0; u < TA; ++u) {
+            have[u] = active && ta + u * tbp < tcount;
+            xh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            xl[u] = xh[u];
+            if (have[u]) {
+                const float4 *xp = reinterpret_cast<const float4 *>(a.xt + (toff + tb + ta + u * tbp) * 8);
+                xh[u] = xp[0];
+                xl[u] = xp[1];
             }
+        }
+        const bool any = have[0];
+        float acc[TA][RC], cmp[TA][RC];
+#pragma unroll
+        for (int u = 0; u < TA; ++u)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) { acc[u][r] = 0.f; cmp[u][r] = 0.f; }
+        for (int64_t e = e0; e < e1;) {
+            load_partner_chunk<kF32Threads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+            const int nchunk = pc.n, total = pc.pre[pc.n];
+            e += nchunk;
+            for (int pos = 0; pos < total; pos += kF32Tile) {
+            const int fill = min(kF32Tile, total - pos);
+            for (int q = tid; q < fill; q += kF32Threads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill; q += kF32Threads) {
                 const float4 *yp = reinterpret_cast<const float4 *>(a.ys + sidx[q] * 8);
@@ -119,35 +127,58 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
                 sq[q] = a.qv[sidx[b] * ldq + c];
             }
             __syncthreads();
-            if (have) {
+            if (any) {
                 for (int b = grp; b < fill; b += groups) {
                     float4 yh = syh[b], yl = syl[b];
-                    float d[3] = {(xh.x - yh.x) + (xl.x - yl.x), (xh.y - yh.y) + (xl.y - yl.y),
-                                  (xh.z - yh.z) + (xl.z - yl.z)};
-                    float kv = kappa_f32<KID, D>(d, a.s_f, a.log_s);
-                    const float *qb = sq + (size_t)b * ldq + ch * RC;
+                    float kv[TA];
 #pragma unroll
-                    for (int r = 0; r < RC; ++r) {
-                        if (KAHAN) {
-                            float y = fmaf(kv, qb[r], -cmp[r]);
-                            float t = acc[r] + y;
-                            cmp[r] = (t - acc[r]) - y;
-                            acc[r] = t;
+                    for (int u = 0; u < TA; ++u) {
+                        float d[3] = {(xh[u].x - yh.x) + (xl[u].x - yl.x), (xh[u].y - yh.y) + (xl[u].y - yl.y),
+                                      (xh[u].z - yh.z) + (xl[u].z - yl.z)};
+                        kv[u] = have[u] ? kappa_f32<KID, D>(d, a.s_f, a.log_s) : 0.f;
+                    }
+                    const float *qb = sq + (size_t)b * ldq + ch * RC;
+                    constexpr int VW = RC >= 4 ? 4 : 1;  // vector width of the loads
+#pragma unroll
+                    for (int r0 = 0; r0 < RC; r0 += VW) {
+                        float qv[VW];
+                        if (VW == 4) {
+                            float4 v = *reinterpret_cast<const float4 *>(qb + r0);
+                            qv[0] = v.x; qv[VW > 1 ? 1 : 0] = v.y; qv[VW > 2 ? 2 : 0] = v.z; qv[VW > 3 ? 3 : 0] = v.w;
                         } else {
-                            acc[r] = fmaf(kv, qb[r], acc[r]);
+                            qv[0] = qb[r0];
                         }
+#pragma unroll
+                        for (int u = 0; u < TA; ++u)
+#pragma unroll
+                            for (int i = 0; i < VW; ++i) {
+                                const int r = r0 + i;
+                                if (KAHAN) {
+                                    float y = fmaf(kv[u], qv[i], -cmp[u][r]);
+                                    float t = acc[u][r] + y;
+                                    cmp[u][r] = (t - acc[u][r]) - y;
+                                    acc[u][r] = t;
+                                } else {
+                                    acc[u][r] = fmaf(kv[u], qv[i], acc[u][r]);
+                                }
+                            }
                     }
                 }
             }
             __syncthreads();
+            }
         }
         for (int gg = 0; gg < groups; ++gg) {
-            if (have && grp == gg) {
+            if (grp == gg) {
 #pragma unroll
-                for (int r = 0; r < RC; ++r) {
-                    double v = KAHAN ? (double)acc[r] - (double)cmp[r] : (double)acc[r];
-                    double *dst = red + (size_t)ta * ldq + ch * RC + r;
-                    *dst = gg == 0 ? v : *dst + v;
+                for (int u = 0; u < TA; ++u) {
+                    if (!have[u]) continue;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        double v = KAHAN ? (double)acc[u][r] - (double)cmp[u][r] : (double)acc[u][r];
+                        double *dst = red + (size_t)(ta + u * tbp) * ldq + ch * RC + r;
+                        *dst = gg == 0 ? v : *dst + v;
+                    }
                 }
             }
             __syncthreads();
@@ -160,16 +191,19 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
 template <int KID, int D, bool KAHAN>
 static void launch_f32(KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
     if (ntn <= 0) return;
+    // two targets per thread where the registers allow it (RC <= 16, no compensation)
+    const int TA = (KAHAN || RC > 16) ? 1 : 2;
     size_t smem = sizeof(float4) * 2 * kF32Tile + sizeof(float) * (size_t)kF32Tile * a.ldq +
-                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * kF32Tile;
+                  sizeof(double) * (size_t)TA * a.tbp * a.ldq + sizeof(int64_t) * kF32Tile;
     void (*kern)(KsumF32Args) = nullptr;
+    constexpr int T2 = KAHAN ? 1 : 2;
     switch (RC) {
-    case 1: kern = ksum_f32_kernel<KID, D, 1, KAHAN>; break;
-    case 2: kern = ksum_f32_kernel<KID, D, 2, KAHAN>; break;
-    case 4: kern = ksum_f32_kernel<KID, D, 4, KAHAN>; break;
-    case 8: kern = ksum_f32_kernel<KID, D, 8, KAHAN>; break;
-    case 16: kern = ksum_f32_kernel<KID, D, 16, KAHAN>; break;
-    default: kern = ksum_f32_kernel<KID, D, 32, KAHAN>; break;
+    case 1: kern = ksum_f32_kernel<KID, D, 1, KAHAN, T2>; break;
+    case 2: kern = ksum_f32_kernel<KID, D, 2, KAHAN, T2>; break;
+    case 4: kern = ksum_f32_kernel<KID, D, 4, KAHAN, T2>; break;
+    case 8: kern = ksum_f32_kernel<KID, D, 8, KAHAN, T2>; break;
+    case 16: kern = ksum_f32_kernel<KID, D, 16, KAHAN, T2>; break;
+    default: kern = ksum_f32_kernel<KID, D, 32, KAHAN, 1>; break;
     }
     allow_max_dynamic_smem((const void *)kern);
     kern<<<(unsigned)ntn, kF32Threads, smem, s>>>(a);

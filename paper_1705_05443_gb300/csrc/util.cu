@@ -70,7 +70,10 @@ void allow_max_dynamic_smem(const void *func) {
     int dev = 0, optin = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, func));
+    int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the same limit
+    CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     done.push_back(func);
 }
 
