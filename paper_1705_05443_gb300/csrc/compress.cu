@@ -554,7 +554,7 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         level_setup_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(a);
         LAUNCHED();
         // threads: one column each where possible
-        const int NT = m_cap <= 64 ? 64 : (m_cap <= 128 ? 128 : 256);
+        const int NT = m_cap <= 64 ? 64 : (m_cap <= 128 ? 128 : (m_cap <= 256 ? 256 : 512));
         size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
                            sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
         size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
@@ -565,7 +565,8 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         bool small_p = h->order <= 16;
         if (NT == 64) kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
         else if (NT == 128) kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
-        else kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
+        else if (NT == 256) kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
+        else kern = small_p ? compress_kernel<512, 16> : compress_kernel<512, kMaxP>;
         allow_max_dynamic_smem((const void *)kern);
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
