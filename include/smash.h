@@ -114,6 +114,27 @@ SMASH_API smash_status smash_build_xy(const double *x, int64_t nx, const double 
                             const smash_options *opt, smash_handle *out);
 
 /*
+ * smash_build_batch -- many independent problems in one representation.
+ * Problem t is the point set points[offsets[t] .. offsets[t+1]) (rows of the
+ * n x dim float64 array, host or device; n = offsets[nproblems]) with X = Y.
+ * Each problem is partitioned in its own bounding cube exactly as
+ * smash_build would partition it alone (Section 3.1), so its tree, lists
+ * (3.3)/(3.4), skeletons and generators (3.17) are those of the problem
+ * built alone; problems never interact.  The nodes of one level of all
+ * problems are processed by the same launches, and smash_matvec* applies
+ * the block-diagonal matrix diag(A^_0, ..., A^_{T-1}) to X (n x nrhs, rows
+ * in the order of points).  The paper treats one problem at a time; the
+ * batch is an extension of this library.
+ *   offsets  host array of nproblems + 1 int64, offsets[0] = 0, strictly
+ *            increasing (every problem has at least one point)
+ * Synchronous.  Errors: SMASH_EINVAL (also for bad offsets), SMASH_ENOMEM,
+ * SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_build_batch(const double *points, const int64_t *offsets, int nproblems, int dim,
+                                         int kernel_id, int leaf_size, int order, double tol,
+                                         const smash_options *opt, smash_handle *out);
+
+/*
  * smash_matvec -- Y = A^ X by the node-wise algorithm of Section 3.4:
  * upward pass (q^_i = V_i^T q, then W_c^T), coupling over L with kernel
  * blocks on skeleton pairs, downward pass (R_c, then U_i), near field over L^-.
@@ -225,9 +246,10 @@ typedef struct {
     int64_t swap_cap_hits;      /* nodes whose swap loop hit its cap */
     int64_t coupling_pairs;     /* sum over (i,j) in L of k_i k_j */
     int64_t near_pairs;         /* sum over (i,j) in L^- of |i| |j| */
-    double lo[3], s;            /* bounding cube [lo, lo + s]^dim */
+    double lo[3], s;            /* bounding cube [lo, lo + s]^dim (of all problems of a batch) */
     double tau, f, tol;
     size_t footprint_bytes;     /* device bytes held by the handle */
+    int64_t nproblems;          /* 1, or the problems of smash_build_batch */
 } smash_info_t;
 
 SMASH_API smash_status smash_info(smash_handle h, smash_info_t *info);
@@ -251,7 +273,11 @@ SMASH_API smash_status smash_info(smash_handle h, smash_info_t *info);
  *   rest_*[sum (m-k)]     the other working-set points, per node ascending
  *   G_*[sum (m-k)k]       per node the (m-k) x k row-major matrix G of (2.11):
  *                         rows follow rest_*, columns follow skel_*
- * (*_col equals *_row when Y = X.)
+ *   node_problem[nnodes]  problem of each node (0 for a single problem)
+ *   problem_cube[nproblems*4]  per problem {lo0, lo1, lo2, s} of its cube
+ * (*_col equals *_row when Y = X.  In a batch the roots of the problems are
+ * the gids 0 .. nproblems-1, and the nodes of problem t, taken in gid order,
+ * are the nodes of that problem built alone.)
  */
 typedef struct {
     int64_t *permx, *permy;
@@ -270,6 +296,8 @@ typedef struct {
     int32_t *m_col, *k_col;
     int64_t *skel_col, *rest_col;
     double *G_col;
+    int32_t *node_problem;
+    double *problem_cube;
 } smash_export_t;
 
 SMASH_API smash_status smash_export(smash_handle h, const smash_export_t *out);

@@ -20,7 +20,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "SmashError", "smash_build", "smash_build_xy", "smash_matvec", "smash_matvec_ex",
+    "SmashError", "smash_build", "smash_build_xy", "smash_build_batch", "smash_matvec", "smash_matvec_ex",
     "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
@@ -58,13 +58,13 @@ class smash_info_t(C.Structure):
                 ("g_col", C.c_int64), ("swaps", C.c_int64), ("swap_cap_hits", C.c_int64),
                 ("coupling_pairs", C.c_int64), ("near_pairs", C.c_int64), ("lo", C.c_double * 3),
                 ("s", C.c_double), ("tau", C.c_double), ("f", C.c_double), ("tol", C.c_double),
-                ("footprint_bytes", C.c_size_t)]
+                ("footprint_bytes", C.c_size_t), ("nproblems", C.c_int64)]
 
 
 _EXPORT_FIELDS = ["permx", "permy", "keyx", "keyy", "lvl_off", "level", "leaf", "parent", "child0",
                   "nchild", "rs", "rc", "cs", "cc", "cell", "adm_ptr", "adm_col", "near_ptr", "near_col",
                   "m_row", "k_row", "skel_row", "rest_row", "G_row", "m_col", "k_col", "skel_col",
-                  "rest_col", "G_col"]
+                  "rest_col", "G_col", "node_problem", "problem_cube"]
 
 
 class smash_export_t(C.Structure):
@@ -95,6 +95,8 @@ def load_library(build: bool = True):
     lib.smash_build.restype = i32
     lib.smash_build_xy.argtypes = [P, i64, P, i64, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
     lib.smash_build_xy.restype = i32
+    lib.smash_build_batch.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
+    lib.smash_build_batch.restype = i32
     lib.smash_matvec.argtypes = [P, P, P, i32]
     lib.smash_matvec.restype = i32
     lib.smash_matvec_ex.argtypes = [P, P, P, i32, i32, P]
@@ -197,6 +199,19 @@ def smash_build_xy(x, y, kernel_id: int, leaf_size: int, order: int, tol: float,
     return h
 
 
+def smash_build_batch(points, offsets, kernel_id: int, leaf_size: int, order: int, tol: float,
+                      tau: float = 0.7, f: float = 2.0, stream=None):
+    """Independent problems points[offsets[t]:offsets[t+1]] in one representation (see smash.h)."""
+    lib = load_library()
+    h = C.c_void_p()
+    opt = smash_options(tau, f, _stream_ptr(stream))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    dim = int(points.shape[1])
+    _check(lib.smash_build_batch(_ptr(points), C.c_void_p(off.ctypes.data), len(off) - 1, dim, kernel_id,
+                                 leaf_size, order, float(tol), C.byref(opt), C.byref(h)))
+    return h
+
+
 def smash_matvec(h, X, Y, nrhs: int | None = None):
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
@@ -248,6 +263,7 @@ def smash_export(h) -> dict:
         "cc": np.empty(nn, np.int64), "cell": np.empty((nn, 3), np.uint64),
         "adm_ptr": np.empty(nn + 1, np.int64), "adm_col": np.empty(i["nadm"], np.int32),
         "near_ptr": np.empty(nn + 1, np.int64), "near_col": np.empty(i["nnear"], np.int32),
+        "node_problem": np.empty(nn, np.int32), "problem_cube": np.empty((i["nproblems"], 4), np.float64),
     }
     for tag in ("row", "col"):
         arrs[f"m_{tag}"] = np.empty(nn, np.int32)
@@ -376,6 +392,15 @@ class H2Matrix:
             self.h = smash_build(x, kernel_id, leaf_size, order, tol)
         else:
             self.h = smash_build_xy(x, y, kernel_id, leaf_size, order, tol, tau, f, stream)
+
+    @classmethod
+    def batch(cls, points, offsets, kernel_id: int, leaf_size: int, order: int, tol: float,
+              tau: float = 0.7, f: float = 2.0, stream=None):
+        """Independent problems points[offsets[t]:offsets[t+1]] (smash_build_batch)."""
+        self = cls.__new__(cls)
+        self.nx = self.ny = _rows(points)
+        self.h = smash_build_batch(points, offsets, kernel_id, leaf_size, order, tol, tau, f, stream)
+        return self
 
     def matvec(self, X, Y=None, precision: int = SMASH_PREC_F64, stream=None):
         if Y is None:

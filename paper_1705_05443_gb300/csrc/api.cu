@@ -171,8 +171,14 @@ smash_status smash_build(const double *points, int dim, int64_t n, int kernel_id
     return smash_build_xy(points, n, nullptr, 0, dim, kernel_id, leaf_size, order, tol, nullptr, out);
 }
 
-smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_t ny, int dim, int kernel_id,
-                            int leaf_size, int order, double tol, const smash_options *opt, smash_handle *out) {
+}  // extern "C"
+
+// Shared by smash_build_xy and smash_build_batch: offsets == nullptr builds
+// one problem (x, y); otherwise x holds nproblems independent problems with
+// X = Y each, problem t owning rows [offsets[t], offsets[t+1]).
+static smash_status build_impl(const double *x, int64_t nx, const double *y, int64_t ny, const int64_t *offsets,
+                               int nproblems, int dim, int kernel_id, int leaf_size, int order, double tol,
+                               const smash_options *opt, smash_handle *out) {
     if (out) *out = nullptr;
     smash_h2 *h = nullptr;
     try {
@@ -196,6 +202,10 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
         if (!(o.f > 1.0)) fail(SMASH_EINVAL, "f must be > 1");
 
         h = new smash_h2();
+        if (offsets) {
+            h->nroots = nproblems;
+            h->tree_off.assign(offsets, offsets + nproblems + 1);
+        }
         h->dim = dim; h->kernel_id = kernel_id; h->leaf_size = leaf_size; h->order = order; h->r = r;
         h->tau = o.tau; h->f = o.f; h->tol = tol;
         h->same = y == nullptr;
@@ -227,7 +237,8 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
         }
         PhaseTimer tm(h->stream, &h->prof_build);
         tm.mark();
-        build_geometry(h, xd, yd, scratch);
+        if (h->nroots > 1) build_geometry_batch(h, xd, scratch);
+        else build_geometry(h, xd, yd, scratch);
         tm.mark();
         build_tree(h, scratch);
         tm.mark();
@@ -263,7 +274,7 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
                 h->ys_x3 = h->mem.alloc<float>((size_t)h->ny * 12);
                 dd_coords3(h->ys, h->ny, h->dd_e, h->ys_x3, h->stream);
             }
-            if (h->L > kDdNormalisedMaxLevels) {
+            if (dd_exact_coupling(h)) {
                 h->row.skel_x3 = h->mem.alloc<float>((size_t)std::max<int64_t>(h->row.total_skel, 1) * 12);
                 dd_coords3(h->row.skel_xyz, h->row.total_skel, h->dd_e, h->row.skel_x3, h->stream);
                 if (!h->same) {
@@ -289,6 +300,35 @@ smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_
         t_last_error = "host allocation failed";
         return SMASH_ENOMEM;
     }
+}
+
+extern "C" {
+
+smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_t ny, int dim, int kernel_id,
+                            int leaf_size, int order, double tol, const smash_options *opt, smash_handle *out) {
+    return build_impl(x, nx, y, ny, nullptr, 1, dim, kernel_id, leaf_size, order, tol, opt, out);
+}
+
+smash_status smash_build_batch(const double *points, const int64_t *offsets, int nproblems, int dim, int kernel_id,
+                               int leaf_size, int order, double tol, const smash_options *opt, smash_handle *out) {
+    if (out) *out = nullptr;
+    if (!offsets || nproblems < 1) {
+        t_last_error = "offsets is NULL or nproblems < 1";
+        return SMASH_EINVAL;
+    }
+    if (offsets[0] != 0) {
+        t_last_error = "offsets[0] must be 0";
+        return SMASH_EINVAL;
+    }
+    for (int t = 0; t < nproblems; ++t)
+        if (offsets[t + 1] <= offsets[t]) {
+            t_last_error = "every problem needs at least one point (offsets strictly increasing)";
+            return SMASH_EINVAL;
+        }
+    const int64_t n = offsets[nproblems];
+    if (nproblems == 1) return build_impl(points, n, nullptr, 0, nullptr, 1, dim, kernel_id, leaf_size, order, tol,
+                                          opt, out);
+    return build_impl(points, n, nullptr, 0, offsets, nproblems, dim, kernel_id, leaf_size, order, tol, opt, out);
 }
 
 smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision, void *stream) {
@@ -354,6 +394,7 @@ smash_status smash_info(smash_handle h, smash_info_t *info) {
     for (int a = 0; a < 3; ++a) info->lo[a] = h->lo[a];
     info->s = h->s; info->tau = h->tau; info->f = h->f; info->tol = h->tol;
     info->footprint_bytes = h->mem.bytes();
+    info->nproblems = h->nroots;
     return SMASH_OK;
 }
 
@@ -383,6 +424,9 @@ smash_status smash_export(smash_handle h, const smash_export_t *o) {
         put(o->adm_col, h->adm_col, h->nadm);
         put(o->near_ptr, h->near_ptr, nn + 1);
         put(o->near_col, h->near_col, h->nnear);
+        put(o->node_problem, h->node_tree, nn);
+        if (o->problem_cube)
+            std::memcpy(o->problem_cube, h->tree_geo_host.data(), h->tree_geo_host.size() * sizeof(double));
         CK(cudaStreamSynchronize(s));
         if (o->rc || o->cc) {
             auto rc = fetch(h->rc, nn, s);

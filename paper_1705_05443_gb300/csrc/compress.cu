@@ -20,8 +20,9 @@ namespace smash {
 
 struct CompressArgs {
     int d, p, r, level;
-    double tol, f, s;
-    double lo[3];
+    double tol, f;
+    const double *geo4;       // per problem {lo0, lo1, lo2, s}: the bounding cube
+    const int32_t *node_tree; // problem of each node
     double anchors[kMaxP];
     double weights[kMaxP];    // w_m = 1 / prod_{n != m} (t_m - t_n)
     int64_t n0, nl;
@@ -128,11 +129,12 @@ __device__ __forceinline__ double lagrange(int p, const double *anch, const doub
 // column c of W = U^^T for the point at sorted index gid, in the cell of node g
 template <int PMAX>
 __device__ void basis_column(const CompressArgs &a, int64_t g, int64_t gid, double *W, int ld, int c) {
-    double h = ldexp(a.s, 1 - a.level);
+    const double *cube = a.geo4 + (int64_t)a.node_tree[g] * 4;
+    double h = ldexp(cube[3], 1 - a.level);
     double half = 0.5 * h;
     double L[3][PMAX];
     for (int ax = 0; ax < a.d; ++ax) {
-        double centre = a.lo[ax] + ((double)a.cell[g * 3 + ax] + 0.5) * h;
+        double centre = cube[ax] + ((double)a.cell[g * 3 + ax] + 0.5) * h;
         double t = (a.pts[gid * 4 + ax] - centre) / half;
         for (int mm = 0; mm < a.p; ++mm) L[ax][mm] = lagrange(a.p, a.anchors, a.weights, mm, t);
     }
@@ -450,14 +452,16 @@ __global__ void compact_skeleton_kernel(int64_t n0, int64_t nl, const int32_t *_
 
 // upper bounds: k <= min(r, count), m <= leaf ? count : sum_children min(r, count_c),
 // |G| <= max_{k <= min(r,m)} (m - k) k
-__global__ void bounds_kernel(int64_t nn, int r, const int32_t *__restrict__ leaf, const int32_t *__restrict__ cnt,
+__global__ void bounds_kernel(int64_t nn, int r, const int32_t *__restrict__ level,
+                              const int32_t *__restrict__ leaf, const int32_t *__restrict__ cnt,
                               const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                               int64_t *__restrict__ kub, int64_t *__restrict__ mub, int64_t *__restrict__ gub) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nn) return;
     int64_t m;
-    if (g == 0) {
-        m = 0;  // the root is never compressed
+    const bool root = level[g] == 1;
+    if (root) {
+        m = 0;  // a root is never compressed
     } else if (leaf[g]) {
         m = cnt[g];
     } else {
@@ -469,7 +473,7 @@ __global__ void bounds_kernel(int64_t nn, int r, const int32_t *__restrict__ lea
     int64_t kb = kh <= kmax ? kh : kmax;
     int64_t gb = (m - kb) * kb;
     if (kh + 1 <= kmax) gb = max(gb, (m - kh - 1) * (kh + 1));
-    kub[g] = g == 0 ? 0 : min((int64_t)r, (int64_t)cnt[g]);
+    kub[g] = root ? 0 : min((int64_t)r, (int64_t)cnt[g]);
     mub[g] = m;
     gub[g] = gb;
 }
@@ -494,7 +498,7 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
     CK(cudaMemsetAsync(S.in_off, 0, nn * 8, st));
     int64_t *kub = scratch.alloc<int64_t>(nn), *mub = scratch.alloc<int64_t>(nn), *gub = scratch.alloc<int64_t>(nn);
     int64_t *tot = scratch.alloc<int64_t>(4);
-    bounds_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, h->r, h->leaf, cnt, h->child0, h->nchild, kub,
+    bounds_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, h->r, h->level, h->leaf, cnt, h->child0, h->nchild, kub,
                                                                  mub, gub);
     LAUNCHED();
     int64_t *kub_off = scratch.alloc<int64_t>(nn);
@@ -539,8 +543,8 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         int m_cap = (int)std::max<int64_t>(lmax[l], 1);
         CompressArgs a;
         a.d = h->dim; a.p = h->order; a.r = h->r; a.level = l;
-        a.tol = h->tol; a.f = h->f; a.s = h->s;
-        for (int i = 0; i < 3; ++i) a.lo[i] = h->lo[i];
+        a.tol = h->tol; a.f = h->f;
+        a.geo4 = h->tree_geo; a.node_tree = h->node_tree;
         for (int i = 0; i < kMaxP; ++i) {
             a.anchors[i] = i < h->order ? h->anchors[i] : 0.0;
             a.weights[i] = i < h->order ? weights[i] : 0.0;

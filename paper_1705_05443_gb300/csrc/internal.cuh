@@ -108,7 +108,17 @@ struct smash_h2 {
     int dim = 0, kernel_id = 0, leaf_size = 0, order = 0, r = 0, same = 1, bits = 0;
     double tau = 0.7, f = 2.0, tol = 1e-8;
     int64_t nx = 0, ny = 0;
+    // bounding cube of all points; for a batch of problems it is the frame of
+    // the matvec coordinates only, each problem keeping its own cube below
     double lo[3] = {0, 0, 0}, s = 1.0;
+    // batch of independent problems (X = Y each): problem t owns the sorted
+    // points [tree_off[t], tree_off[t+1]) and the root node t; one problem
+    // otherwise (nroots = 1, tree_geo = node_tree = nullptr)
+    int64_t nroots = 1;
+    std::vector<int64_t> tree_off;
+    std::vector<double> tree_geo_host;  // nroots x {lo0, lo1, lo2, s}
+    double *tree_geo = nullptr;         // device copy
+    int32_t *node_tree = nullptr;       // problem of each node
     double anchors[smash::kMaxP];
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -148,6 +158,7 @@ namespace smash {
 
 // phases of the build (each in its own translation unit)
 void build_geometry(smash_h2 *h, const double *x_dev, const double *y_dev, Arena &scratch);
+void build_geometry_batch(smash_h2 *h, const double *x_dev, Arena &scratch);
 void build_tree(smash_h2 *h, Arena &scratch);
 void build_lists(smash_h2 *h, Arena &scratch);
 void build_compression(smash_h2 *h, Arena &scratch);
@@ -166,6 +177,9 @@ void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st
 int dd_exact_exponent(double s);
 // the double-float coupling uses normalised two-float coordinates up to this depth
 constexpr int kDdNormalisedMaxLevels = 10;
+// whether the double-float coupling takes the exact three-float coordinates:
+// deep trees, and batches (whose cells are finer than the frame's levels)
+inline bool dd_exact_coupling(const smash_h2 *h) { return h->L > kDdNormalisedMaxLevels || h->nroots > 1; }
 // pass helpers shared by the matvec variants
 void matvec_gather(const smash_h2 *h, const double *X, int nrhs, int ldq, double *qs, cudaStream_t s);
 void matvec_upward(const smash_h2 *h, const double *qs, double *qhat, int ldq, cudaStream_t s);

@@ -292,12 +292,12 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         LAUNCHED();
     }
     tm.mark();
-    if (h->nnodes > 1) {
+    if (h->nnodes > h->nroots) {
         KsumArgs a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nnodes - 1, h->r, RC, s);
+        ksum(h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     for (int l = 2; l <= h->L; ++l) {
@@ -404,12 +404,12 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X, double *Y, int nrhs,
         upward_kernel<<<(unsigned)nl, 256, 0, s>>>(p);
         LAUNCHED();
     }
-    if (h->nnodes > 1) {
+    if (h->nnodes > h->nroots) {
         KsumArgs a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nnodes - 1, h->r, RC, s);
+        ksum(h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     for (int l = 2; l <= h->L; ++l) {
         int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;

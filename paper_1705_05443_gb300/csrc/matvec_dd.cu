@@ -411,15 +411,15 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
     matvec_upward(h, qs, qhat, ldq, s);
     dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
     tm.mark();
-    if (h->nnodes > 1) {
+    if (h->nnodes > h->nroots) {
         KsumDDArgs a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
-        const bool exact = h->L > kDdNormalisedMaxLevels;
+        const bool exact = dd_exact_coupling(h);
         a.xt = exact ? R.skel_x3 : R.skel_dd;
         a.ys = exact ? Cs.skel_x3 : Cs.skel_dd;
         a.qv = qhat2; a.out = zhat; a.scale = exact ? ldexp(1.0, -h->dd_e) : scale; a.ldq = ldq;
-        ksum_dd(h->kernel_id, h->dim, exact, a, h->nnodes - 1, h->r, RC, s);
+        ksum_dd(h->kernel_id, h->dim, exact, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

@@ -295,12 +295,12 @@ void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
     matvec_upward(h, qs, qhat, ldq, s);
     to_f32(qhat, Cs.total_skel * ldq, qhat1, s);
     tm.mark();
-    if (h->nnodes > 1) {
+    if (h->nnodes > h->nroots) {
         KsumF32Args a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.qv = qhat1; a.out = zhat; a.ldq = ldq;
-        ksum_f32(h, false, a, h->nnodes - 1, h->r, RC, s);
+        ksum_f32(h, false, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

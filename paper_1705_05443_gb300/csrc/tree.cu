@@ -146,6 +146,9 @@ void build_geometry(smash_h2 *h, const double *x_dev, const double *y_dev, Arena
     if (hbad) fail(SMASH_EINVAL, "non-finite point coordinate");
     for (int a = 0; a < 3; ++a) h->lo[a] = hg.lo[a];
     h->s = hg.s;
+    h->tree_geo_host = {hg.lo[0], hg.lo[1], hg.lo[2], hg.s};
+    h->tree_geo = h->mem.alloc<double>(4);
+    CK(cudaMemcpyAsync(h->tree_geo, h->tree_geo_host.data(), 4 * sizeof(double), cudaMemcpyHostToDevice, s));
     sort_side(h, x_dev, h->nx, g, h->keyx, h->permx, h->xs, scratch);
     if (h->same) {
         h->keyy = h->keyx;
@@ -159,11 +162,148 @@ void build_geometry(smash_h2 *h, const double *x_dev, const double *y_dev, Arena
     scratch.free(bad);
 }
 
+// ------------------------------------------------------------------ batch of problems
+// One CTA per problem: its bounding cube exactly as for a single problem
+// (componentwise min and max, largest extent times (1 + 2^-40)).
+__global__ void bbox_segment_kernel(const double *__restrict__ p, const int64_t *__restrict__ off, int d,
+                                    double *__restrict__ geo7, int *__restrict__ bad) {
+    const int64_t t = blockIdx.x;
+    const int64_t i0 = off[t], i1 = off[t + 1];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nonfinite = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+        for (int a = 0; a < d; ++a) {
+            double v = p[i * d + a];
+            if (!isfinite(v)) nonfinite = 1;
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    for (int a = 0; a < d; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    __shared__ double slo[32][3], shi[32][3];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) { slo[w][a] = lo[a]; shi[w][a] = hi[a]; }
+    if (nonfinite) atomicOr(bad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L[3], H[3];
+        for (int a = 0; a < 3; ++a) {
+            L[a] = INFINITY; H[a] = -INFINITY;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) { L[a] = fmin(L[a], slo[ww][a]); H[a] = fmax(H[a], shi[ww][a]); }
+        }
+        double ext = 0.0;
+        for (int a = 0; a < d; ++a)
+            if (H[a] - L[a] > ext) ext = H[a] - L[a];
+        for (int a = d; a < 3; ++a) { L[a] = 0.0; H[a] = 0.0; }
+        double *o = geo7 + t * 7;
+        for (int a = 0; a < 3; ++a) { o[a] = L[a]; o[3 + a] = H[a]; }
+        o[6] = ext > 0.0 ? ext * (1.0 + 0x1p-40) : 1.0;
+    }
+}
+
+// Morton key of every point in the cube of its own problem; tkey = problem.
+__global__ void morton_batch_kernel(const double *__restrict__ p, int64_t n, int d, int b,
+                                    const int64_t *__restrict__ off, int ntrees, const double *__restrict__ geo4,
+                                    uint64_t *__restrict__ keys, uint64_t *__restrict__ tkeys,
+                                    int32_t *__restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = ntrees - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const double *g = geo4 + (int64_t)lo * 4;
+    uint64_t q[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) q[a] = quantize(p[i * d + a], g[a], g[3], b);
+    uint64_t key = 0;
+    for (int l = 0; l < b; ++l)
+        for (int a = 0; a < d; ++a) key = (key << 1) | ((q[a] >> (b - 1 - l)) & 1u);
+    keys[i] = key;
+    tkeys[i] = (uint64_t)lo;
+    idx[i] = (int32_t)i;
+}
+
+__global__ void gather_u64_kernel(const uint64_t *__restrict__ src, const int32_t *__restrict__ idx, int64_t n,
+                                  uint64_t *__restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+// Points of all problems sorted by (problem, Morton key): a stable sort by
+// key, then a stable sort by problem.
+void build_geometry_batch(smash_h2 *h, const double *x_dev, Arena &scratch) {
+    cudaStream_t s = h->stream;
+    const int64_t T = h->nroots, n = h->nx;
+    const int d = h->dim;
+    int64_t *off = scratch.alloc<int64_t>(T + 1);
+    CK(cudaMemcpyAsync(off, h->tree_off.data(), (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    double *geo7 = scratch.alloc<double>(T * 7);
+    int *bad = scratch.alloc<int>(1);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    bbox_segment_kernel<<<(unsigned)T, 256, 0, s>>>(x_dev, off, d, geo7, bad);
+    LAUNCHED();
+    std::vector<double> g7((size_t)T * 7);
+    int hbad = 0;
+    CK(cudaMemcpyAsync(g7.data(), geo7, T * 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hbad) fail(SMASH_EINVAL, "non-finite point coordinate");
+    h->tree_geo_host.assign((size_t)T * 4, 0.0);
+    double flo[3] = {INFINITY, INFINITY, INFINITY}, fhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < T; ++t) {
+        for (int a = 0; a < 3; ++a) {
+            h->tree_geo_host[t * 4 + a] = g7[t * 7 + a];
+            flo[a] = std::min(flo[a], g7[t * 7 + a]);
+            fhi[a] = std::max(fhi[a], g7[t * 7 + 3 + a]);
+        }
+        h->tree_geo_host[t * 4 + 3] = g7[t * 7 + 6];
+    }
+    // the matvec frame: the cube of all problems
+    double ext = 0.0;
+    for (int a = 0; a < d; ++a) ext = std::max(ext, fhi[a] - flo[a]);
+    for (int a = 0; a < 3; ++a) h->lo[a] = a < d ? flo[a] : 0.0;
+    h->s = ext > 0.0 ? ext * (1.0 + 0x1p-40) : 1.0;
+    h->tree_geo = h->mem.alloc<double>(T * 4);
+    CK(cudaMemcpyAsync(h->tree_geo, h->tree_geo_host.data(), T * 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+
+    uint64_t *kraw = scratch.alloc<uint64_t>(n), *tk = scratch.alloc<uint64_t>(n), *tk2 = scratch.alloc<uint64_t>(n);
+    int32_t *idx = scratch.alloc<int32_t>(n);
+    h->keyx = h->mem.alloc<uint64_t>(n);
+    h->permx = h->mem.alloc<int64_t>(n);
+    h->xs = h->mem.alloc<double>((size_t)n * 4);
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    morton_batch_kernel<<<blocks, 256, 0, s>>>(x_dev, n, d, h->bits, off, (int)T, h->tree_geo, kraw, tk, idx);
+    LAUNCHED();
+    CK(cudaMemcpyAsync(h->keyx, kraw, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    radix_sort(h->keyx, idx, n, d * h->bits, s, scratch);
+    gather_u64_kernel<<<blocks, 256, 0, s>>>(tk, idx, n, tk2);
+    LAUNCHED();
+    int tbits = 1;
+    while ((1ll << tbits) < T) ++tbits;
+    radix_sort(tk2, idx, n, tbits, s, scratch);
+    gather_u64_kernel<<<blocks, 256, 0, s>>>(kraw, idx, n, h->keyx);
+    LAUNCHED();
+    gather_points_kernel<<<blocks, 256, 0, s>>>(x_dev, n, d, idx, h->permx, h->xs);
+    LAUNCHED();
+    h->keyy = h->keyx;
+    h->permy = h->permx;
+    h->ys = h->xs;
+    scratch.free(kraw); scratch.free(tk); scratch.free(tk2); scratch.free(idx);
+    scratch.free(off); scratch.free(geo7); scratch.free(bad);
+}
+
 // ------------------------------------------------------------------ tree
 struct NodeArrays {
     int32_t *level, *leaf, *parent, *child0, *nchild, *rc, *cc;
     int64_t *rs, *cs;
     uint64_t *cell;
+    int32_t *tree;
 };
 
 // first position in [lo, hi) whose digit (key >> shift) & mask is >= c
@@ -225,6 +365,7 @@ __global__ void emit_children_kernel(NodeArrays A, int64_t n0, int64_t nl, int d
     int64_t c = nnext0 + choff[i] + before;
     A.level[c] = l + 1;
     A.parent[c] = (int32_t)g;
+    A.tree[c] = A.tree[g];
     A.child0[c] = -1;
     A.nchild[c] = 0;
     A.rs[c] = crs[t];
@@ -258,6 +399,7 @@ static void grow_nodes(NodeArrays &A, int64_t used, int64_t cap, Arena &mem, cud
     grow(A.rs, used, cap, mem, s);
     grow(A.cs, used, cap, mem, s);
     grow(A.cell, used * 3, cap * 3, mem, s);
+    grow(A.tree, used, cap, mem, s);
 }
 
 __global__ void leaf_list_kernel(const int32_t *__restrict__ leaf, int64_t n, const int64_t *__restrict__ pos,
@@ -275,31 +417,43 @@ void build_tree(smash_h2 *h, Arena &scratch) {
     cudaStream_t s = h->stream;
     int d = h->dim, b = h->bits, nd = 1 << d;
     NodeArrays A{};
-    int64_t cap = 1024;
+    // level 1: one root per problem
+    const int64_t R = h->nroots;
+    int64_t cap = std::max<int64_t>(1024, 2 * R);
     grow_nodes(A, 0, cap, h->mem, s);
-    // root
     {
-        int32_t lv = 1, pa = -1, c0 = -1, nc = 0;
-        int32_t rc = (int32_t)h->nx, cc = (int32_t)h->ny;
-        int64_t z = 0;
-        int64_t big = std::max(h->nx, h->ny);
-        int32_t lf = !(big > h->leaf_size && 1 <= b);
-        uint64_t cell0[3] = {0, 0, 0};
-        CK(cudaMemcpyAsync(A.level, &lv, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.parent, &pa, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.child0, &c0, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.nchild, &nc, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.rc, &rc, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.cc, &cc, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.rs, &z, 8, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.cs, &z, 8, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.leaf, &lf, 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(A.cell, cell0, 24, cudaMemcpyHostToDevice, s));
+        std::vector<int32_t> lv(R, 1), pa(R, -1), c0(R, -1), nc(R, 0), rc(R), cc(R), lf(R), tr(R);
+        std::vector<int64_t> rs(R), cs(R);
+        std::vector<uint64_t> cell0((size_t)R * 3, 0);
+        for (int64_t t = 0; t < R; ++t) {
+            if (R == 1) {
+                rs[t] = cs[t] = 0;
+                rc[t] = (int32_t)h->nx;
+                cc[t] = (int32_t)h->ny;
+            } else {
+                rs[t] = cs[t] = h->tree_off[t];
+                rc[t] = cc[t] = (int32_t)(h->tree_off[t + 1] - h->tree_off[t]);
+            }
+            int64_t big = std::max(rc[t], cc[t]);
+            lf[t] = !(big > h->leaf_size && 1 <= b);
+            tr[t] = (int32_t)t;
+        }
+        CK(cudaMemcpyAsync(A.level, lv.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.parent, pa.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.child0, c0.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.nchild, nc.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.rc, rc.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.cc, cc.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.rs, rs.data(), R * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.cs, cs.data(), R * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.leaf, lf.data(), R * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.cell, cell0.data(), R * 24, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(A.tree, tr.data(), R * 4, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
     }
     h->lvl_off.assign(1, 0);
-    h->lvl_off.push_back(1);
-    int64_t total = 1;
+    h->lvl_off.push_back(R);
+    int64_t total = R;
     int l = 1;
     int64_t *next_total = scratch.alloc<int64_t>(1);
     for (;;) {
@@ -338,7 +492,7 @@ void build_tree(smash_h2 *h, Arena &scratch) {
     h->L = l;
     h->nnodes = total;
     h->level = A.level; h->leaf = A.leaf; h->parent = A.parent; h->child0 = A.child0; h->nchild = A.nchild;
-    h->rs = A.rs; h->cs = A.cs; h->rc = A.rc; h->cc = A.cc; h->cell = A.cell;
+    h->rs = A.rs; h->cs = A.cs; h->rc = A.rc; h->cc = A.cc; h->cell = A.cell; h->node_tree = A.tree;
     // leaf list
     int64_t *pos = scratch.alloc<int64_t>(total);
     exclusive_scan<int32_t>(h->leaf, pos, total, nullptr, next_total, s, scratch);
@@ -347,9 +501,9 @@ void build_tree(smash_h2 *h, Arena &scratch) {
     h->leaf_list = h->mem.alloc<int32_t>(std::max<int64_t>(h->nleaves, 1));
     leaf_list_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->leaf, total, pos, h->leaf_list);
     LAUNCHED();
-    h->nonroot_list = h->mem.alloc<int32_t>(std::max<int64_t>(total - 1, 1));
-    if (total > 1) {
-        iota_kernel<<<(unsigned)((total - 1 + 255) / 256), 256, 0, s>>>(h->nonroot_list, total - 1, 1);
+    h->nonroot_list = h->mem.alloc<int32_t>(std::max<int64_t>(total - R, 1));
+    if (total > R) {
+        iota_kernel<<<(unsigned)((total - R + 255) / 256), 256, 0, s>>>(h->nonroot_list, total - R, (int32_t)R);
         LAUNCHED();
     }
     scratch.free(pos);
@@ -443,15 +597,22 @@ static void to_csr(smash_h2 *h, uint64_t *pairs, int64_t n, int nb, int64_t *&pt
 
 void build_lists(smash_h2 *h, Arena &scratch) {
     cudaStream_t s = h->stream;
-    NodeArrays A{h->level, h->leaf, h->parent, h->child0, h->nchild, h->rc, h->cc, h->rs, h->cs, h->cell};
+    NodeArrays A{h->level, h->leaf, h->parent, h->child0, h->nchild, h->rc, h->cc, h->rs, h->cs, h->cell,
+                 h->node_tree};
     int nb = 1;
     while ((1ll << nb) < h->nnodes) ++nb;
     int64_t cap_a = 1 << 16, cap_n = 1 << 16;
     uint64_t *adm = scratch.alloc<uint64_t>(cap_a), *near = scratch.alloc<uint64_t>(cap_n);
     int64_t na = 0, nn = 0;
-    uint64_t *fr = scratch.alloc<uint64_t>(1);
-    CK(cudaMemsetAsync(fr, 0, 8, s));  // (root, root)
-    int64_t nf = 1;
+    // traversal from (root, root) of every problem
+    int64_t nf = h->nroots;
+    uint64_t *fr = scratch.alloc<uint64_t>(nf);
+    {
+        std::vector<uint64_t> f0((size_t)nf);
+        for (int64_t t = 0; t < nf; ++t) f0[t] = ((uint64_t)t << nb) | (uint64_t)t;
+        CK(cudaMemcpyAsync(fr, f0.data(), nf * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
     int64_t *tot = scratch.alloc<int64_t>(5);  // [0] adm base, [1] near base, [2..4] totals
     CK(cudaMemsetAsync(tot, 0, 5 * sizeof(int64_t), s));
     while (nf > 0) {

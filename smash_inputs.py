@@ -24,6 +24,7 @@ __all__ = [
     "jittered_grid",
     "rhs",
     "sample_rows",
+    "batched_problems",
     "WORKLOADS",
     "make_workload",
 ]
@@ -114,6 +115,41 @@ def sample_rows(n: int, count: int, seed: int) -> np.ndarray:
     return np.sort(_rng(seed).choice(n, size=count, replace=False)).astype(np.int64)
 
 
+def batched_problems(count: int, seed: int, n_lo: int = 1024, n_hi: int = 32768) -> list:
+    """`count` independent problems of the batched-trees workload.  Per
+    problem: N = floor(exp(U(ln n_lo, ln n_hi))) (log-uniform), dimension 2
+    or 3 with probability 1/2 each (kernel log|x-y| in 2D, 1/|x-y| in 3D),
+    points uniform in the unit cube or from a 4-component Gaussian mixture
+    with sigma 0.1, with probability 1/2 each.  Returns a list of dicts with
+    keys d, kernel, kind and x (N x d float64)."""
+    g = _rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(np.floor(np.exp(g.uniform(np.log(n_lo), np.log(n_hi)))))
+        n = min(max(n, n_lo), n_hi)
+        d = 2 if g.random() < 0.5 else 3
+        kind = "cube" if g.random() < 0.5 else "mixture"
+        sub = int(g.integers(0, 2 ** 31 - 1))
+        x = uniform_cube(n, d, sub) if kind == "cube" else gaussian_mixture(n, d, sub, ncomp=4, sigma=0.1)
+        out.append(dict(d=d, kernel=KERNEL_LOG if d == 2 else KERNEL_INVR, kind=kind, x=x))
+    return out
+
+
+def group_by_dimension(problems: list) -> dict:
+    """Concatenates the problems of each dimension: {d: (points, offsets,
+    kernel, indices into `problems`)}, problems kept in their order."""
+    groups = {}
+    for i, p in enumerate(problems):
+        groups.setdefault(p["d"], []).append(i)
+    out = {}
+    for d, idx in sorted(groups.items()):
+        xs = [problems[i]["x"] for i in idx]
+        off = np.zeros(len(xs) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([len(x) for x in xs])
+        out[d] = (np.ascontiguousarray(np.concatenate(xs, axis=0)), off, problems[idx[0]]["kernel"], idx)
+    return out
+
+
 # Kernel identifiers shared by convention (the C-ABI header and the oracle
 # each define their own copy of these numbers).
 KERNEL_LOG, KERNEL_INVR, KERNEL_YUKAWA, KERNEL_CAUCHY = 0, 1, 2, 3
@@ -132,6 +168,8 @@ WORKLOADS = {
     # 3D mixed precision on the sphere with clustered caps
     "sphere_yukawa_1m": dict(kind="sphere", n=1 << 20, d=3, kernel=KERNEL_YUKAWA, leaf=128,
                              order=5, tol=1e-8, nrhs=32, index=2),
+    # 512 independent problems (batched_problems), FP32 matvec with 8 RHS each
+    "batched_512": dict(kind="batch", count=512, leaf=64, order=4, tol=1e-8, nrhs=8, index=3),
 }
 
 
@@ -143,6 +181,15 @@ def make_workload(name: str, rep: int = 0, n: int | None = None):
     if n is not None:
         w["n"] = int(n)
     seed = w["index"] * 1000 + rep
+    if w["kind"] == "batch":
+        # `n` overrides the number of problems
+        if n is not None:
+            w["count"] = int(n)
+        w["problems"] = batched_problems(w["count"], seed)
+        w["groups"] = group_by_dimension(w["problems"])
+        w["n"] = sum(len(p["x"]) for p in w["problems"])
+        w["q"] = {d: rhs(len(g[0]), w["nrhs"], seed + 500 + d) for d, g in w["groups"].items()}
+        return w
     if w["kind"] == "cube":
         x = uniform_cube(w["n"], w["d"], seed)
         y = None

@@ -103,3 +103,22 @@ def test_free_and_info_accept_null():
     lib.smash_free(None)
     assert lib.smash_footprint_bytes(None) == 0
     assert lib.smash_info(None, None) == 1
+
+
+@pytest.mark.parametrize("offsets,msg", [
+    ([], "nproblems"),
+    ([1, 5], "offsets[0]"),
+    ([0, 5, 5], "at least one point"),
+    ([0, 7, 3], "at least one point"),
+])
+def test_batch_offsets_are_validated_before_any_device_work(offsets, msg):
+    import numpy as np
+    lib = sm.load_library()
+    x = np.random.default_rng(1).random((16, 3))
+    off = np.asarray(offsets, dtype=np.int64)
+    h = C.c_void_p(12345)
+    st = lib.smash_build_batch(C.c_void_p(x.ctypes.data), C.c_void_p(off.ctypes.data) if off.size else None,
+                               max(len(off) - 1, 0), 3, 1, 8, 3, 1e-8, None, C.byref(h))
+    assert st == 1
+    assert h.value is None
+    assert msg in lib.smash_last_error().decode()
