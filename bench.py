@@ -195,6 +195,92 @@ def run_serving(sm, torch, requests: int, rate: float, seed: int, precision: int
     }
 
 
+def run_batched(sm, torch, dev, steps: int = 2, warmup: int = 1, reps: int = 10) -> dict:
+    """The batched-trees workload: 512 independent problems (2D log and 3D
+    1/r, uniform or Gaussian-mixture clouds), one batch representation per
+    dimension built concurrently on two streams, then the FP32 matvec with 8
+    RHS of each.  A step is both builds plus both matvecs; points/s counts
+    every point of every problem.  Also times repeated applies of the built
+    batches through smash_matvec_ex and through the CUDA-graph replay."""
+    import threading
+    wl = si.make_workload("batched_512")
+    groups = wl["groups"]
+    ds = sorted(groups)
+    xs = {d: torch.from_numpy(groups[d][0]).to(dev) for d in ds}
+    qs = {d: torch.from_numpy(wl["q"][d]).to(dev) for d in ds}
+    zs = {d: torch.empty_like(qs[d]) for d in ds}
+    streams = {d: torch.cuda.Stream(dev) for d in ds}
+    handles = {}
+    errors = []
+
+    def one(d):
+        try:
+            x, off, kid, _ = groups[d]
+            h = sm.smash_build_batch(xs[d], off, kid, wl["leaf"], wl["order"], wl["tol"], stream=streams[d])
+            sm.smash_matvec_ex(h, qs[d], zs[d], sm.SMASH_PREC_F32, stream=streams[d])
+            handles[d] = h
+        except Exception as e:  # reported by the caller
+            errors.append(e)
+
+    def step():
+        ts = [threading.Thread(target=one, args=(d,)) for d in ds]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        torch.cuda.synchronize()
+        if errors:
+            raise errors[0]
+
+    times = []
+    for i in range(warmup + steps):
+        if i >= warmup:
+            sm.smash_set_autotune(False)
+        for h in handles.values():
+            sm.smash_free(h)
+        handles.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step()
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    n = wl["n"]
+    info = {d: sm.smash_info(handles[d]) for d in ds}
+    # repeated applies of the resident batches
+    s = streams[ds[0]]
+    plain, graph = [], []
+    for mode, out in (("plain", plain), ("graph", graph)):
+        for d in ds:
+            fn = sm.smash_matvec_ex if mode == "plain" else sm.smash_matvec_graph
+            fn(handles[d], qs[d], zs[d], sm.SMASH_PREC_F32, stream=s)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            for d in ds:
+                fn = sm.smash_matvec_ex if mode == "plain" else sm.smash_matvec_graph
+                fn(handles[d], qs[d], zs[d], sm.SMASH_PREC_F32, stream=s)
+        e1.record(s)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / reps)
+    for h in handles.values():
+        sm.smash_free(h)
+    med = statistics.median(times)
+    return {
+        "workload": "batched_512: 512 problems, N log-uniform in [1024, 32768], 2D log|x-y| / 3D 1/|x-y|, "
+                    "uniform cube or 4-component Gaussian mixture (sigma 0.1), leaf 64, order 4, tol 1e-8, "
+                    "FP64 build, FP32 matvec with 8 RHS",
+        "problems": int(sum(info[d]["nproblems"] for d in ds)), "points": int(n),
+        "value": n / med, "unit": "points/s (build + FP32 matvec of all problems)",
+        "ms_per_step": 1e3 * med, "steps": steps, "timing": "host wall clock around the synchronous builds",
+        "per_dimension": {str(d): {"problems": info[d]["nproblems"], "points": info[d]["nx"],
+                                   "levels": info[d]["levels"], "nodes": info[d]["nnodes"]} for d in ds},
+        "resident_apply_ms": {"smash_matvec_ex": plain[0], "smash_matvec_graph": graph[0],
+                              "note": "both batches, FP32, 8 RHS, mean of %d applies" % reps},
+    }
+
+
 def bench_reference(args, w):
     ws, rank = _dist()
     if rank != 0:
@@ -260,9 +346,14 @@ def bench_ours(args, w):
         return h
 
     sm.smash_set_profiling(True)
+    # the first warm-up step times the candidate launch shapes of every tuned
+    # site (autotuner); later steps use the recorded choices
+    sm.smash_set_autotune(args.autotune)
     for _ in range(args.warmup):
         sm.smash_free(step())
+        sm.smash_set_autotune(False)
     torch.cuda.synchronize()
+    tune_entries = sm.smash_autotune_entries()
     info = None
     coupling_ms, step_ms = [], []
     sampler = ClockSampler(local)
@@ -369,6 +460,11 @@ def bench_ours(args, w):
         wdef = (f"per kernel entry {DD_MAC_OPS}*nrhs + {DD_EVAL_OPS} FP32 instructions of the "
                 "double-float algorithm (error-free products and sums)")
     achieved = cpl_work / (cpl_ms / 1e3) / 1e12
+    batched = None
+    if args.batched:
+        sm.smash_set_autotune(args.autotune)
+        batched = run_batched(sm, torch, dev)
+        sm.smash_set_autotune(False)
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(sm, torch, args.serve_requests, 200.0, 4000, prec)
@@ -401,6 +497,9 @@ def bench_ours(args, w):
                 "h2d_bytes_per_step": int(x_np.nbytes + q_np.nbytes), "d2h_bytes_per_step": int(q_np.nbytes)},
         "gpu_launches": int(launches / args.steps),
         "serving": serving,
+        "batched": batched,
+        "autotune": {"enabled": bool(args.autotune), "entries_after_warmup": tune_entries,
+                     "entries": sm.smash_autotune_entries()},
         "clocks": clocks,
         "wall_s": wall,
         "peaks_file": peak_src,
@@ -428,6 +527,10 @@ def main():
     ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64", "f32"],
                     help="matvec arithmetic: double-float kernel sums (FP64-accurate), plain FP64, or "
                          "mixed precision FP32")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the batched-trees measurement")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the default launch shapes instead of tuning them in the first warm-up step")
     args = ap.parse_args()
     w = dict(si.WORKLOADS[args.workload])
     if args.n:

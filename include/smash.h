@@ -181,6 +181,21 @@ SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *
 #define SMASH_NOALLOC_SCRATCH_BYTES (64u << 20)
 SMASH_API smash_status smash_matvec_noalloc(smash_handle h, const double *X, double *Y, int nrhs, void *stream);
 
+/*
+ * smash_matvec_graph -- smash_matvec_ex for device buffers X and Y, replayed
+ * from a CUDA graph: the first call with a given (X, Y, nrhs, precision)
+ * runs the matvec once, then captures its launches and stream-ordered
+ * scratch allocations into a graph kept by the handle; every call launches
+ * that graph on `stream` (NULL: the handle's stream, and the call waits for
+ * completion).  The paper has no counterpart; this serves repeated applies
+ * of a resident representation.  Results equal smash_matvec_ex's with the
+ * same precision.  Errors: as smash_matvec_ex; SMASH_EINVAL for host
+ * buffers.  smash_matvec_graph_count returns the graphs a handle holds.
+ */
+SMASH_API smash_status smash_matvec_graph(smash_handle h, const double *X, double *Y, int nrhs, int precision,
+                                          void *stream);
+SMASH_API int smash_matvec_graph_count(smash_handle h);
+
 /* Releases the handle and its device memory; NULL-safe; waits for the
  * handle's pending work first. */
 SMASH_API void smash_free(smash_handle h);
@@ -312,6 +327,30 @@ SMASH_API size_t smash_predict_footprint(int64_t n, int dim, int leaf_size, int 
 
 /* The farfield-rank heuristic of Section 6.1 for tolerance eps and ratio tau. */
 SMASH_API int smash_suggest_rank(double eps, double tau);
+
+/*
+ * Autotuning (an extension of this library; the paper has no counterpart).
+ * Launch sites with several valid configurations -- the threads per node CTA
+ * of the compression, the source tile and target block of the kernel sums --
+ * look their choice up in a process-wide table keyed by the launch shape.
+ * With smash_set_autotune(1), a shape without an entry is timed once for
+ * every candidate (CUDA events on the launching stream; not while the stream
+ * is being captured into a graph) and the fastest is recorded.  All
+ * candidates compute the same results: the compression bit for bit, the
+ * kernel sums up to the order of their partial sums.  The table is saved to
+ * and loaded from a flat JSON file; the environment variable
+ * SMASH_AUTOTUNE_CACHE names a file loaded at the first lookup.
+ *   smash_autotune_load    returns the entries read, or -1 (file missing or
+ *                          malformed; the table is unchanged)
+ *   smash_autotune_save    SMASH_EINVAL if the file cannot be written
+ *   smash_autotune_lookup  1 and *value if key has an entry, else 0
+ */
+SMASH_API void smash_set_autotune(int on);
+SMASH_API int smash_autotune_load(const char *path);
+SMASH_API smash_status smash_autotune_save(const char *path);
+SMASH_API int smash_autotune_entries(void);
+SMASH_API void smash_autotune_clear(void);
+SMASH_API int smash_autotune_lookup(const char *key, int *value);
 
 /* Message of the last failed call on this host thread ("" if none). */
 SMASH_API const char *smash_last_error(void);

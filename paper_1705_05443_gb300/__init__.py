@@ -21,6 +21,8 @@ from . import _build
 
 __all__ = [
     "SmashError", "smash_build", "smash_build_xy", "smash_build_batch", "smash_matvec", "smash_matvec_ex",
+    "smash_matvec_graph", "smash_matvec_graph_count", "smash_set_autotune", "smash_autotune_load",
+    "smash_autotune_save", "smash_autotune_entries", "smash_autotune_clear", "smash_autotune_lookup",
     "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
@@ -97,6 +99,22 @@ def load_library(build: bool = True):
     lib.smash_build_xy.restype = i32
     lib.smash_build_batch.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
     lib.smash_build_batch.restype = i32
+    lib.smash_matvec_graph.argtypes = [P, P, P, i32, i32, P]
+    lib.smash_matvec_graph.restype = i32
+    lib.smash_matvec_graph_count.argtypes = [P]
+    lib.smash_matvec_graph_count.restype = i32
+    lib.smash_set_autotune.argtypes = [i32]
+    lib.smash_set_autotune.restype = None
+    lib.smash_autotune_load.argtypes = [C.c_char_p]
+    lib.smash_autotune_load.restype = i32
+    lib.smash_autotune_save.argtypes = [C.c_char_p]
+    lib.smash_autotune_save.restype = i32
+    lib.smash_autotune_entries.argtypes = []
+    lib.smash_autotune_entries.restype = i32
+    lib.smash_autotune_clear.argtypes = []
+    lib.smash_autotune_clear.restype = None
+    lib.smash_autotune_lookup.argtypes = [C.c_char_p, C.POINTER(i32)]
+    lib.smash_autotune_lookup.restype = i32
     lib.smash_matvec.argtypes = [P, P, P, i32]
     lib.smash_matvec.restype = i32
     lib.smash_matvec_ex.argtypes = [P, P, P, i32, i32, P]
@@ -232,6 +250,45 @@ def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
     _check(lib.smash_matvec_noalloc(h, _ptr(X), _ptr(Y), nrhs, _stream_ptr(stream)))
     return Y
+
+
+def smash_matvec_graph(h, X, Y, precision: int = SMASH_PREC_F64, stream=None, nrhs: int | None = None):
+    """Y = A^ X replayed from a CUDA graph captured at the first call (device X, Y)."""
+    lib = load_library()
+    nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check(lib.smash_matvec_graph(h, _ptr(X), _ptr(Y), nrhs, precision, _stream_ptr(stream)))
+    return Y
+
+
+def smash_matvec_graph_count(h) -> int:
+    return int(load_library().smash_matvec_graph_count(h))
+
+
+def smash_set_autotune(on: bool):
+    load_library().smash_set_autotune(1 if on else 0)
+
+
+def smash_autotune_load(path: str) -> int:
+    return int(load_library().smash_autotune_load(str(path).encode()))
+
+
+def smash_autotune_save(path: str):
+    lib = load_library()
+    _check(lib.smash_autotune_save(str(path).encode()))
+
+
+def smash_autotune_entries() -> int:
+    return int(load_library().smash_autotune_entries())
+
+
+def smash_autotune_clear():
+    load_library().smash_autotune_clear()
+
+
+def smash_autotune_lookup(key: str):
+    v = C.c_int32(0)
+    ok = load_library().smash_autotune_lookup(key.encode(), C.byref(v))
+    return int(v.value) if ok else None
 
 
 def smash_free(h):
@@ -411,6 +468,9 @@ class H2Matrix:
         if precision == SMASH_PREC_F64 and stream is None:
             return smash_matvec(self.h, X, Y)
         return smash_matvec_ex(self.h, X, Y, precision, stream)
+
+    def matvec_graph(self, X, Y, precision: int = SMASH_PREC_F64, stream=None):
+        return smash_matvec_graph(self.h, X, Y, precision, stream)
 
     def info(self) -> dict:
         return smash_info(self.h)

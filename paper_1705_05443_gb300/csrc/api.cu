@@ -107,6 +107,7 @@ void build_stats(smash_h2 *h, Arena &scratch) {
 static void destroy(smash_h2 *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
     h->mem.release();
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -331,15 +332,37 @@ smash_status smash_build_batch(const double *points, const int64_t *offsets, int
     return build_impl(points, n, nullptr, 0, offsets, nproblems, dim, kernel_id, leaf_size, order, tol, opt, out);
 }
 
+}  // extern "C"
+
+namespace smash {
+
+void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision) {
+    if (!h) fail(SMASH_EINVAL, "handle is NULL");
+    if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
+    if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
+    if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2 && precision != SMASH_PREC_F32)
+        fail(SMASH_EINVAL, "unknown precision %d", precision);
+    if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
+        fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
+}
+
+void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int precision, cudaStream_t s,
+                Profile *prof) {
+    if (precision == SMASH_PREC_F32X2)
+        matvec_dd(h, X, Y, nrhs, s, prof);
+    else if (precision == SMASH_PREC_F32)
+        matvec_f32(h, X, Y, nrhs, s, prof);
+    else
+        matvec_f64(h, X, Y, nrhs, s, prof);
+}
+
+}  // namespace smash
+
+extern "C" {
+
 smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision, void *stream) {
     try {
-        if (!h) fail(SMASH_EINVAL, "handle is NULL");
-        if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
-        if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
-        if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2 && precision != SMASH_PREC_F32)
-            fail(SMASH_EINVAL, "unknown precision %d", precision);
-        if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
-            fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
+        check_matvec_args(h, X, Y, nrhs, precision);
         cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
         Arena io(s);
         const double *Xd = X;
@@ -352,12 +375,7 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         }
         if (yhost) Yd = io.alloc<double>((size_t)h->nx * nrhs);
         h->prof_mv.on = profiling_enabled();
-        if (precision == SMASH_PREC_F32X2)
-            matvec_dd(h, Xd, Yd, nrhs, s, &h->prof_mv);
-        else if (precision == SMASH_PREC_F32)
-            matvec_f32(h, Xd, Yd, nrhs, s, &h->prof_mv);
-        else
-            matvec_f64(h, Xd, Yd, nrhs, s, &h->prof_mv);
+        run_matvec(h, Xd, Yd, nrhs, precision, s, &h->prof_mv);
         if (yhost) CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         io.release();
         if (yhost || !stream) CK(cudaStreamSynchronize(s));

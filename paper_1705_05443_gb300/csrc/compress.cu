@@ -557,39 +557,68 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         a.m_cap = m_cap;
         level_setup_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(a);
         LAUNCHED();
-        // threads: one column each where possible
-        const int NT = m_cap <= 64 ? 64 : (m_cap <= 128 ? 128 : (m_cap <= 256 ? 256 : 512));
-        size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
-                           sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
-        size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
-        a.w_in_smem = (base_smem + w_bytes) <= 160 * 1024;
-        size_t smem = base_smem + (a.w_in_smem ? w_bytes : 0);
-        a.slot_doubles = (a.w_in_smem ? 0 : (int64_t)h->r * m_cap) + (int64_t)h->r * h->r;
-        void (*kern)(CompressArgs) = nullptr;
-        bool small_p = h->order <= 16;
-        if (NT == 64) kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
-        else if (NT == 128) kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
-        else if (NT == 256) kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
-        else kern = small_p ? compress_kernel<512, 16> : compress_kernel<512, kMaxP>;
-        allow_max_dynamic_smem((const void *)kern);
-        int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-        if (per_sm < 1) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", smem);
-        int64_t grid = std::min<int64_t>(nl, (int64_t)per_sm * h->num_sms);
-        // keep the concurrent node matrices of a global-slot level inside the L2
-        if (!a.w_in_smem) {
-            int64_t fit = (int64_t)(64ll << 20) / (a.slot_doubles * (int64_t)sizeof(double));
-            grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(fit, h->num_sms)));
+        // The CTA size is a free choice: every candidate computes the same bits
+        // (each column is reduced by one thread in the oracle's order).  The
+        // default gives one column per thread up to 512 threads.
+        const bool small_p = h->order <= 16;
+        struct Plan {
+            void (*kern)(CompressArgs);
+            size_t smem;
+            int64_t grid;
+            bool w_in_smem;
+            int64_t slot_doubles;
+        };
+        auto plan = [&](int NT, Plan &pl) -> bool {
+            size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
+                               sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
+            size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
+            pl.w_in_smem = (base_smem + w_bytes) <= 160 * 1024;
+            pl.smem = base_smem + (pl.w_in_smem ? w_bytes : 0);
+            pl.slot_doubles = (pl.w_in_smem ? 0 : (int64_t)h->r * m_cap) + (int64_t)h->r * h->r;
+            if (NT == 64) pl.kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
+            else if (NT == 128) pl.kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
+            else if (NT == 256) pl.kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
+            else pl.kern = small_p ? compress_kernel<512, 16> : compress_kernel<512, kMaxP>;
+            allow_max_dynamic_smem((const void *)pl.kern);
+            int per_sm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kern, NT, pl.smem));
+            if (per_sm < 1) return false;
+            pl.grid = std::min<int64_t>(nl, (int64_t)per_sm * h->num_sms);
+            // keep the concurrent node matrices of a global-slot level inside the L2
+            if (!pl.w_in_smem) {
+                int64_t fit = (int64_t)(64ll << 20) / (pl.slot_doubles * (int64_t)sizeof(double));
+                pl.grid = std::max<int64_t>(1, std::min<int64_t>(pl.grid, std::max<int64_t>(fit, h->num_sms)));
+            }
+            return true;
+        };
+        const int NT_def = m_cap <= 64 ? 64 : (m_cap <= 128 ? 128 : (m_cap <= 256 ? 256 : 512));
+        std::vector<int> cands;
+        Plan pdef;
+        if (!plan(NT_def, pdef)) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", pdef.smem);
+        for (int nt = 64; nt <= 512; nt *= 2) {
+            Plan pl;
+            if (plan(nt, pl)) cands.push_back(nt);
         }
-        int64_t need = grid * a.slot_doubles;
-        if (need > work_cap) {
-            if (work) scratch.free(work);
-            work = scratch.alloc<double>(need);
-            work_cap = need;
-        }
-        a.work = work;
-        kern<<<(unsigned)grid, NT, smem, st>>>(a);
-        LAUNCHED();
+        auto run = [&](int NT) {
+            Plan pl;
+            plan(NT, pl);
+            CompressArgs b = a;
+            b.w_in_smem = pl.w_in_smem;
+            b.slot_doubles = pl.slot_doubles;
+            int64_t need = pl.grid * pl.slot_doubles;
+            if (need > work_cap) {
+                if (work) scratch.free(work);
+                work = scratch.alloc<double>(need);
+                work_cap = need;
+            }
+            b.work = work;
+            pl.kern<<<(unsigned)pl.grid, NT, pl.smem, st>>>(b);
+            LAUNCHED();
+        };
+        char key[128];
+        std::snprintf(key, sizeof(key), "compress/sm%d/d%d/p%d/m%lld/n%lld", h->num_sms, h->dim, h->order,
+                      pow2_at_least(m_cap), pow2_at_least(nl));
+        tune_choose(key, cands, NT_def, st, run);
         exclusive_scan<int32_t>(S.k + n0, S.sk_off + n0, nl, base, base, st, scratch);
         compact_skeleton_kernel<<<(unsigned)nl, 128, 0, st>>>(n0, nl, S.k, S.sk_off, S.loc_off, S.skg_tmp, pts,
                                                                S.skel_gidx, S.skel_xyz);

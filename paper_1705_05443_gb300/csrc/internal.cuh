@@ -3,8 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <functional>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -104,6 +106,10 @@ struct Profile {
 
 }  // namespace smash
 
+namespace smash {
+struct GraphCache;
+}
+
 struct smash_h2 {
     int dim = 0, kernel_id = 0, leaf_size = 0, order = 0, r = 0, same = 1, bits = 0;
     double tau = 0.7, f = 2.0, tol = 1e-8;
@@ -152,6 +158,7 @@ struct smash_h2 {
     int64_t swaps = 0, swap_cap_hits = 0, coupling_pairs = 0, near_pairs = 0;
     int64_t rest_row = 0, g_row = 0, rest_col = 0, g_col = 0;  // exact sums of m-k and (m-k)k
     smash::Profile prof_build, prof_mv;
+    smash::GraphCache *graphs = nullptr;  // captured matvecs (smash_matvec_graph)
 };
 
 namespace smash {
@@ -193,6 +200,28 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X_dev, double *Y_dev, i
                         void *scratch, size_t scratch_bytes);
 
 bool profiling_enabled();
+
+// argument checks of the matvec entry points (fail() on bad input) and the
+// precision dispatch they share
+void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision);
+void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int precision, cudaStream_t s,
+                Profile *prof);
+void destroy_graphs(smash_h2 *h);
+
+// ---------------------------------------------------------------- autotuning
+// tune_choose launches the recorded choice of `key` (or `dflt`); with tuning
+// on and no record, it first times launch(c) for every candidate c on stream
+// s (launch must be idempotent), records the fastest and launches it.
+bool tune_active(cudaStream_t s);
+bool tune_find(const std::string &key, int &value);
+void tune_put(const std::string &key, int value);
+int tune_choose(const std::string &key, const std::vector<int> &cands, int dflt, cudaStream_t s,
+                const std::function<void(int)> &launch);
+inline long long pow2_at_least(long long v) {
+    long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
 
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in
 // maximum, once per kernel.  The limit is a per-function setting shared by all

@@ -118,6 +118,7 @@ struct KsumArgs {
     const double *qv;  // source vectors, ldq
     double *out;       // target vectors, ldq
     int ldq, nchunks, tbp, groups;
+    int tile;          // source points staged per round (<= kKsTile)
 };
 
 constexpr int kKsThreads = 256;
@@ -127,10 +128,11 @@ template <int KID, int RC>
 __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
-    P4 *sy = reinterpret_cast<P4 *>(smraw);                     // kKsTile
-    double *sq = reinterpret_cast<double *>(sy + kKsTile);                // kKsTile * ldq
-    double *red = sq + (size_t)kKsTile * a.ldq;                          // tbp * ldq
-    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);  // kKsTile
+    const int tile = a.tile;                                   // <= kKsTile
+    P4 *sy = reinterpret_cast<P4 *>(smraw);                     // tile
+    double *sq = reinterpret_cast<double *>(sy + tile);                   // tile * ldq
+    double *red = sq + (size_t)tile * a.ldq;                             // tbp * ldq
+    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);  // tile
 
     const int64_t g = a.tnodes[blockIdx.x];
     const int T = a.t_cnt[g];
@@ -167,8 +169,8 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
             load_partner_chunk<kKsThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
             const int nchunk = pc.n, total = pc.pre[pc.n];
             e += nchunk;
-            for (int pos = 0; pos < total; pos += kKsTile) {
-            const int fill = min(kKsTile, total - pos);
+            for (int pos = 0; pos < total; pos += tile) {
+            const int fill = min(tile, total - pos);
             for (int q = tid; q < fill; q += kKsThreads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill; q += kKsThreads) sy[q] = reinterpret_cast<const P4 *>(a.ys)[sidx[q]];
@@ -216,8 +218,8 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
 template <int KID>
 static void launch_ksum(KsumArgs a, int64_t ntn, int RC, cudaStream_t s) {
     if (ntn <= 0) return;
-    size_t smem = sizeof(P4) * kKsTile + sizeof(double) * ((size_t)kKsTile * a.ldq + (size_t)a.tbp * a.ldq) +
-                  sizeof(int64_t) * kKsTile;
+    size_t smem = sizeof(P4) * a.tile + sizeof(double) * ((size_t)a.tile * a.ldq + (size_t)a.tbp * a.ldq) +
+                  sizeof(int64_t) * a.tile;
     void (*kern)(KsumArgs) = nullptr;
     switch (RC) {
     case 1: kern = ksum_f64_kernel<KID, 1>; break;
@@ -232,20 +234,40 @@ static void launch_ksum(KsumArgs a, int64_t ntn, int RC, cudaStream_t s) {
     LAUNCHED();
 }
 
-static void ksum(int kid, KsumArgs a, int64_t ntn, int max_targets, int RC, cudaStream_t s) {
-    // thread shape: tbp targets x nchunks RHS chunks x groups over sources
-    a.nchunks = a.ldq / RC;
-    int tbp = 32;
-    while (tbp < max_targets && tbp * 2 * a.nchunks <= kKsThreads) tbp *= 2;
-    if (tbp * a.nchunks > kKsThreads) tbp = std::max(1, kKsThreads / a.nchunks);
-    a.tbp = tbp;
-    a.groups = std::max(1, kKsThreads / (tbp * a.nchunks));
+static void ksum_launch(int kid, KsumArgs a, int64_t ntn, int RC, cudaStream_t s) {
     switch (kid) {
     case SMASH_K_LOG: launch_ksum<SMASH_K_LOG>(a, ntn, RC, s); break;
     case SMASH_K_INVR: launch_ksum<SMASH_K_INVR>(a, ntn, RC, s); break;
     case SMASH_K_YUKAWA: launch_ksum<SMASH_K_YUKAWA>(a, ntn, RC, s); break;
     default: launch_ksum<SMASH_K_CAUCHY1D>(a, ntn, RC, s); break;
     }
+}
+
+// Thread shape: tbp targets x nchunks RHS chunks x groups over sources.  With
+// tuning (h != nullptr), bit 0 of the choice halves the source tile and bit 1
+// halves the target block cap.
+static void ksum(const smash_h2 *h, int kid, KsumArgs a, int64_t ntn, int max_targets, int RC, cudaStream_t s) {
+    a.nchunks = a.ldq / RC;
+    int tbp = 32;
+    while (tbp < max_targets && tbp * 2 * a.nchunks <= kKsThreads) tbp *= 2;
+    if (tbp * a.nchunks > kKsThreads) tbp = std::max(1, kKsThreads / a.nchunks);
+    auto run = [&](int c) {
+        KsumArgs b = a;
+        b.tile = (c & 1) ? kKsTile / 2 : kKsTile;
+        b.tbp = (c & 2) ? tbp / 2 : tbp;
+        b.groups = std::max(1, kKsThreads / (b.tbp * b.nchunks));
+        ksum_launch(kid, b, ntn, RC, s);
+    };
+    if (!h) {
+        run(0);
+        return;
+    }
+    std::vector<int> cands = {0, 1};
+    if (tbp >= 64) { cands.push_back(2); cands.push_back(3); }
+    char key[160];
+    std::snprintf(key, sizeof(key), "ksum_f64/sm%d/k%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, kid, RC, a.ldq,
+                  pow2_at_least(max_targets), pow2_at_least(ntn));
+    tune_choose(key, cands, 0, s, run);
 }
 
 // ------------------------------------------------------------------ driver
@@ -281,7 +303,7 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs; a.ys = h->ys; a.qv = qs; a.out = zs; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum(h, h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
     for (int l = h->L; l >= 2; --l) {
@@ -297,7 +319,7 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum(h, h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     for (int l = 2; l <= h->L; ++l) {
@@ -395,7 +417,7 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X, double *Y, int nrhs,
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs; a.ys = h->ys; a.qv = qs; a.out = zs; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum(nullptr, h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     for (int l = h->L; l >= 2; --l) {
         int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
@@ -409,7 +431,7 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X, double *Y, int nrhs,
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
-        ksum(h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum(nullptr, h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     for (int l = 2; l <= h->L; ++l) {
         int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;

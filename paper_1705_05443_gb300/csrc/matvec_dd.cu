@@ -199,6 +199,7 @@ struct KsumDDArgs {
     double *out;       // target vectors (FP64), ldq
     double scale;      // 1/s
     int ldq, nchunks, tbp, groups;
+    int tile;          // source points staged per round (<= kDdTile)
 };
 
 constexpr int kDdThreads = 256;
@@ -209,9 +210,10 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
     constexpr int NC = EXACT ? 3 : 2;                                 // float4 per point
-    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // kDdTile * NC
-    float2 *sq = reinterpret_cast<float2 *>(sy + NC * kDdTile);      // kDdTile * ldq
-    double *red = reinterpret_cast<double *>(sq + (size_t)kDdTile * a.ldq);  // tbp * ldq
+    const int tile = a.tile;                                         // <= kDdTile
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // tile * NC
+    float2 *sq = reinterpret_cast<float2 *>(sy + NC * tile);         // tile * ldq
+    double *red = reinterpret_cast<double *>(sq + (size_t)tile * a.ldq);  // tbp * ldq
     int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);
 
     const int64_t g = a.tnodes[blockIdx.x];
@@ -251,13 +253,13 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
             load_partner_chunk<kDdThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
             const int nchunk = pc.n, total = pc.pre[pc.n];
             e += nchunk;
-            for (int pos = 0; pos < total; pos += kDdTile) {
-            const int fill = min(kDdTile, total - pos);
+            for (int pos = 0; pos < total; pos += tile) {
+            const int fill = min(tile, total - pos);
             for (int q = tid; q < fill; q += kDdThreads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill * NC; q += kDdThreads) {
                 int b = q / NC, c = q % NC;
-                sy[c * kDdTile + b] = reinterpret_cast<const float4 *>(a.ys + sidx[b] * (4 * NC))[c];
+                sy[c * tile + b] = reinterpret_cast<const float4 *>(a.ys + sidx[b] * (4 * NC))[c];
             }
             for (int q = tid; q < fill * ldq; q += kDdThreads) {
                 int b = q / ldq, c = q % ldq;
@@ -268,12 +270,12 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
                 for (int b = grp; b < fill; b += groups) {
                     float dh[3], dl[3];
                     if (EXACT) {
-                        float4 yh = sy[b], ym = sy[kDdTile + b], yl = sy[2 * kDdTile + b];
+                        float4 yh = sy[b], ym = sy[tile + b], yl = sy[2 * tile + b];
                         diff3(xc[0].x, xc[1].x, xc[2 % NC].x, yh.x, ym.x, yl.x, dh[0], dl[0]);
                         diff3(xc[0].y, xc[1].y, xc[2 % NC].y, yh.y, ym.y, yl.y, dh[1], dl[1]);
                         diff3(xc[0].z, xc[1].z, xc[2 % NC].z, yh.z, ym.z, yl.z, dh[2], dl[2]);
                     } else {
-                        float4 yh = sy[b], yl = sy[kDdTile + b];
+                        float4 yh = sy[b], yl = sy[tile + b];
                         dh[0] = xc[0].x - yh.x; dh[1] = xc[0].y - yh.y; dh[2] = xc[0].z - yh.z;
                         dl[0] = xc[1].x - yl.x; dl[1] = xc[1].y - yl.y; dl[2] = xc[1].z - yl.z;
                     }
@@ -330,8 +332,8 @@ template <int KID, int D, bool EXACT>
 static void launch_dd(KsumDDArgs a, int64_t ntn, int RC, cudaStream_t s) {
     if (ntn <= 0) return;
     constexpr int NC = EXACT ? 3 : 2;
-    size_t smem = sizeof(float4) * NC * kDdTile + sizeof(float2) * (size_t)kDdTile * a.ldq +
-                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * kDdTile;
+    size_t smem = sizeof(float4) * NC * a.tile + sizeof(float2) * (size_t)a.tile * a.ldq +
+                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * a.tile;
     void (*kern)(KsumDDArgs) = nullptr;
     switch (RC) {
     case 1: kern = ksum_dd_kernel<KID, D, 1, EXACT>; break;
@@ -359,18 +361,31 @@ static void ksum_dd_dispatch(int kid, int dim, KsumDDArgs a, int64_t ntn, int RC
     }
 }
 
-static void ksum_dd(int kid, int dim, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
+// Tuned shape: bit 0 halves the source tile, bit 1 halves the cap of the
+// target block (more source groups per target).
+static void ksum_dd(const smash_h2 *h, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
                     cudaStream_t s) {
+    const int kid = h->kernel_id, dim = h->dim;
     a.nchunks = a.ldq / RC;
     int tbp = 32;
     while (tbp < max_targets && tbp * 2 * a.nchunks <= kDdThreads) tbp *= 2;
     if (tbp * a.nchunks > kDdThreads) tbp = std::max(1, kDdThreads / a.nchunks);
-    a.tbp = tbp;
-    a.groups = std::max(1, kDdThreads / (tbp * a.nchunks));
-    if (exact)
-        ksum_dd_dispatch<true>(kid, dim, a, ntn, RC, s);
-    else
-        ksum_dd_dispatch<false>(kid, dim, a, ntn, RC, s);
+    std::vector<int> cands = {0, 1};
+    if (tbp >= 64) { cands.push_back(2); cands.push_back(3); }
+    auto run = [&](int c) {
+        KsumDDArgs b = a;
+        b.tile = (c & 1) ? kDdTile / 2 : kDdTile;
+        b.tbp = (c & 2) ? tbp / 2 : tbp;
+        b.groups = std::max(1, kDdThreads / (b.tbp * b.nchunks));
+        if (exact)
+            ksum_dd_dispatch<true>(kid, dim, b, ntn, RC, s);
+        else
+            ksum_dd_dispatch<false>(kid, dim, b, ntn, RC, s);
+    };
+    char key[160];
+    std::snprintf(key, sizeof(key), "ksum_dd/sm%d/k%d/d%d/x%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, kid, dim,
+                  exact ? 1 : 0, RC, a.ldq, pow2_at_least(max_targets), pow2_at_least(ntn));
+    tune_choose(key, cands, 0, s, run);
 }
 
 // ------------------------------------------------------------------ transfers (FP64)
@@ -405,7 +420,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs_x3; a.ys = h->ys_x3; a.qv = qs2; a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq;
-        ksum_dd(h->kernel_id, h->dim, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum_dd(h, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
     matvec_upward(h, qs, qhat, ldq, s);
@@ -419,7 +434,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         a.xt = exact ? R.skel_x3 : R.skel_dd;
         a.ys = exact ? Cs.skel_x3 : Cs.skel_dd;
         a.qv = qhat2; a.out = zhat; a.scale = exact ? ldexp(1.0, -h->dd_e) : scale; a.ldq = ldq;
-        ksum_dd(h->kernel_id, h->dim, exact, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum_dd(h, exact, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

@@ -37,6 +37,7 @@ struct KsumF32Args {
     float s_f;         // s, for the Yukawa kernel
     float log_s;       // log s, for the log kernel
     int ldq, nchunks, tbp;
+    int tile;          // source points staged per round (<= kF32Tile)
 };
 
 constexpr int kF32Threads = 256;
@@ -64,10 +65,11 @@ template <int KID, int D, int RC, bool KAHAN, int TA>
 __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
-    float4 *syh = reinterpret_cast<float4 *>(smraw);             // kF32Tile
-    float4 *syl = syh + kF32Tile;                                 // kF32Tile
-    float *sq = reinterpret_cast<float *>(syl + kF32Tile);        // kF32Tile * ldq
-    double *red = reinterpret_cast<double *>(sq + (size_t)kF32Tile * a.ldq);  // TA * tbp * ldq
+    const int tile = a.tile;                                      // <= kF32Tile
+    float4 *syh = reinterpret_cast<float4 *>(smraw);             // tile
+    float4 *syl = syh + tile;                                     // tile
+    float *sq = reinterpret_cast<float *>(syl + tile);            // tile * ldq
+    double *red = reinterpret_cast<double *>(sq + (size_t)tile * a.ldq);  // TA * tbp * ldq
     int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)TA * a.tbp * a.ldq);
 
     const int64_t g = a.tnodes[blockIdx.x];
@@ -113,8 +115,8 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
             load_partner_chunk<kF32Threads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
             const int nchunk = pc.n, total = pc.pre[pc.n];
             e += nchunk;
-            for (int pos = 0; pos < total; pos += kF32Tile) {
-            const int fill = min(kF32Tile, total - pos);
+            for (int pos = 0; pos < total; pos += tile) {
+            const int fill = min(tile, total - pos);
             for (int q = tid; q < fill; q += kF32Threads) sidx[q] = chunk_source(pc, pos + q);
             __syncthreads();
             for (int q = tid; q < fill; q += kF32Threads) {
@@ -193,8 +195,8 @@ static void launch_f32(KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
     if (ntn <= 0) return;
     // two targets per thread where the registers allow it (RC <= 16, no compensation)
     const int TA = (KAHAN || RC > 16) ? 1 : 2;
-    size_t smem = sizeof(float4) * 2 * kF32Tile + sizeof(float) * (size_t)kF32Tile * a.ldq +
-                  sizeof(double) * (size_t)TA * a.tbp * a.ldq + sizeof(int64_t) * kF32Tile;
+    size_t smem = sizeof(float4) * 2 * a.tile + sizeof(float) * (size_t)a.tile * a.ldq +
+                  sizeof(double) * (size_t)TA * a.tbp * a.ldq + sizeof(int64_t) * a.tile;
     void (*kern)(KsumF32Args) = nullptr;
     constexpr int T2 = KAHAN ? 1 : 2;
     switch (RC) {
@@ -238,15 +240,26 @@ static void ksum_f32(const smash_h2 *h, bool kahan, KsumF32Args a, int64_t ntn, 
     int tbp = 32;
     while (tbp < max_targets && tbp * 2 * a.nchunks <= kF32Threads) tbp *= 2;
     if (tbp * a.nchunks > kF32Threads) tbp = std::max(1, kF32Threads / a.nchunks);
-    a.tbp = tbp;
     const bool mult = h->kernel_id == SMASH_K_INVR || h->kernel_id == SMASH_K_CAUCHY1D;
     a.scale = mult ? 1.0 / h->s : 1.0;
     a.s_f = (float)h->s;
     a.log_s = (float)log(h->s);
-    if (kahan)
-        dispatch_f32<true>(h->kernel_id, h->dim, a, ntn, RC, s);
-    else
-        dispatch_f32<false>(h->kernel_id, h->dim, a, ntn, RC, s);
+    // tuned shape: bit 0 halves the source tile, bit 1 halves the target block cap
+    std::vector<int> cands = {0, 1};
+    if (tbp >= 64) { cands.push_back(2); cands.push_back(3); }
+    auto run = [&](int c) {
+        KsumF32Args b = a;
+        b.tile = (c & 1) ? kF32Tile / 2 : kF32Tile;
+        b.tbp = (c & 2) ? tbp / 2 : tbp;
+        if (kahan)
+            dispatch_f32<true>(h->kernel_id, h->dim, b, ntn, RC, s);
+        else
+            dispatch_f32<false>(h->kernel_id, h->dim, b, ntn, RC, s);
+    };
+    char key[160];
+    std::snprintf(key, sizeof(key), "ksum_f32/sm%d/k%d/d%d/c%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, h->kernel_id,
+                  h->dim, kahan ? 1 : 0, RC, a.ldq, pow2_at_least(max_targets), pow2_at_least(ntn));
+    tune_choose(key, cands, 0, s, run);
 }
 
 __global__ void to_f32_kernel(const double *__restrict__ in, int64_t n, float *__restrict__ out) {

@@ -122,3 +122,34 @@ def test_batch_offsets_are_validated_before_any_device_work(offsets, msg):
     assert st == 1
     assert h.value is None
     assert msg in lib.smash_last_error().decode()
+
+
+def test_autotune_table_round_trips_through_a_file(tmp_path):
+    """The autotune table is host state: load, look up, save and reload
+    without a device."""
+    sm.smash_autotune_clear()
+    assert sm.smash_autotune_entries() == 0
+    src = tmp_path / "in.json"
+    src.write_text('{"smash_autotune": 1, "entries": {"compress/sm152/d3/p4/m512/n1024": 256,\n'
+                   ' "ksum_dd/sm152/k1/d3/x1/rc16/ld16/t128/n32768": 3}}')
+    assert sm.smash_autotune_load(str(src)) == 2
+    assert sm.smash_autotune_lookup("compress/sm152/d3/p4/m512/n1024") == 256
+    assert sm.smash_autotune_lookup("no/such/key") is None
+    out = tmp_path / "out.json"
+    sm.smash_autotune_save(str(out))
+    sm.smash_autotune_clear()
+    assert sm.smash_autotune_load(str(out)) == 2
+    assert sm.smash_autotune_lookup("ksum_dd/sm152/k1/d3/x1/rc16/ld16/t128/n32768") == 3
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"entries": {"a": x}}')
+    assert sm.smash_autotune_load(str(bad)) == -1
+    assert sm.smash_autotune_load(str(tmp_path / "missing.json")) == -1
+    assert sm.smash_autotune_entries() == 2   # unchanged by the failed loads
+    sm.smash_autotune_clear()
+
+
+def test_matvec_graph_rejects_null_handle():
+    lib = sm.load_library()
+    assert lib.smash_matvec_graph(None, None, None, 1, 0, None) == 1
+    assert "NULL" in lib.smash_last_error().decode()
+    assert lib.smash_matvec_graph_count(None) == 0
