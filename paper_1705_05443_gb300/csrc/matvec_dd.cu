@@ -52,6 +52,19 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
     e = b - (s - a);
 }
 
+// The same s and e as two_sum: with the operands ordered by magnitude the
+// three-operation form above is exact (Dekker), so the error term -- which
+// is unique -- comes out bit for bit equal.  The compare and the two selects
+// issue on the ALU pipe, leaving three operations on the FP32 pipe instead
+// of six.
+__device__ __forceinline__ void two_sum_ordered(float a, float b, float &s, float &e) {
+    const bool a_big = fabsf(a) >= fabsf(b);
+    const float big = a_big ? a : b;
+    const float small = a_big ? b : a;
+    s = a + b;
+    e = small - (s - big);
+}
+
 // ------------------------------------------------------------------ conversions
 // per point: (hi x, hi y, hi z, 0, lo x, lo y, lo z, 0) of x'' = 1 + (x - lo)/s
 __global__ void dd_coords_kernel(const double *__restrict__ pts, int64_t n, double lo0, double lo1, double lo2,
@@ -125,11 +138,11 @@ static void dd_split(const double *in, int64_t n, float2 *out, cudaStream_t st) 
 __device__ __forceinline__ void diff3(float xh, float xm, float xl, float yh, float ym, float yl, float &dh,
                                       float &dl) {
     float a, ea, b, eb;
-    two_sum(xh, -yh, a, ea);
-    two_sum(xm, -ym, b, eb);
+    two_sum_ordered(xh, -yh, a, ea);
+    two_sum_ordered(xm, -ym, b, eb);
     float c = xl - yl;
     float s, t;
-    two_sum(a, b, s, t);
+    two_sum_ordered(a, b, s, t);
     t = t + ((ea + eb) + c);
     fast_two_sum(s, t, dh, dl);
 }
@@ -167,8 +180,8 @@ __device__ __forceinline__ void kappa_dd(const float *dh, const float *dl, float
         }
     }
     float s1, t1, rh, t2;
-    two_sum(p[0], p[1], s1, t1);
-    two_sum(s1, p[2], rh, t2);
+    two_sum_ordered(p[0], p[1], s1, t1);
+    two_sum_ordered(s1, p[2], rh, t2);
     float rl = ((e[0] + e[1]) + (e[2] + t1)) + t2;
     fast_two_sum(rh, rl, rh, rl);
     if (rh == 0.f) { kh = 0.f; kl = 0.f; return; }
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
                         pe = fmaf(kh, qq.y, pe);
                         pe = fmaf(kl, qq.x, pe);
                         float s, t;
-                        two_sum(ah[r], p, s, t);
+                        two_sum_ordered(ah[r], p, s, t);
                         ah[r] = s;
                         al[r] = al[r] + (t + pe);
                     }
