@@ -68,10 +68,17 @@ enum {
                              pipe (each value hi + lo floats, error-free products and sums,
                              ~1e-12 relative to FP64); transfers FP64.  Kernels 1/|x-y| and
                              1/(x-y) only. */
-    SMASH_PREC_F32 = 2    /* mixed precision: coupling and near field in FP32 (kernel entries,
+    SMASH_PREC_F32 = 2,   /* mixed precision: coupling and near field in FP32 (kernel entries,
                              products, sums; the near field with Kahan-compensated sums),
                              differences from two-float coordinates; transfers FP64.
                              ~1e-7..1e-6 relative to FP64.  All kernels. */
+    /* As SMASH_PREC_F32, with the coupling products (3.19) on the tensor cores: each
+     * coupling block is evaluated in FP32 straight into the operand registers of
+     * warp-level MMAs and multiplied with q^ in the stated format, accumulating in FP32.
+     * The near field stays FP32 with compensated sums.  All kernels. */
+    SMASH_PREC_TF32 = 3,  /* TF32 products (10-bit mantissas); ~1e-4 relative to FP64 */
+    SMASH_PREC_BF16 = 4,  /* BF16 products (7-bit mantissas); ~1e-3 relative to FP64 */
+    SMASH_PREC_TF32X3 = 5 /* split TF32 (hi*hi + hi*lo + lo*hi): FP32-level, ~1e-6 */
 };
 
 typedef struct {

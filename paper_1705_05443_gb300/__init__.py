@@ -28,6 +28,7 @@ __all__ = [
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
     "smash_last_profile", "H2Matrix", "SmashServer", "load_library", "library_path",
     "SMASH_K_LOG", "SMASH_K_INVR", "SMASH_K_YUKAWA", "SMASH_K_CAUCHY1D", "SMASH_PREC_F64", "SMASH_PREC_F32X2", "SMASH_PREC_F32",
+    "SMASH_PREC_TF32", "SMASH_PREC_BF16", "SMASH_PREC_TF32X3",
     "PROFILE_PHASES",
 ]
 
@@ -35,6 +36,9 @@ SMASH_K_LOG, SMASH_K_INVR, SMASH_K_YUKAWA, SMASH_K_CAUCHY1D = 0, 1, 2, 3
 SMASH_PREC_F64 = 0
 SMASH_PREC_F32X2 = 1
 SMASH_PREC_F32 = 2
+SMASH_PREC_TF32 = 3
+SMASH_PREC_BF16 = 4
+SMASH_PREC_TF32X3 = 5
 PROFILE_PHASES = ("geometry", "tree", "lists", "compression", "gather", "near", "upward", "coupling",
                   "downward", "scatter")
 _STATUS = {0: "SMASH_OK", 1: "SMASH_EINVAL", 2: "SMASH_ENOMEM", 3: "SMASH_ECUDA", 4: "SMASH_ETIMEOUT",

@@ -340,7 +340,7 @@ void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int 
     if (!h) fail(SMASH_EINVAL, "handle is NULL");
     if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
     if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
-    if (precision != SMASH_PREC_F64 && precision != SMASH_PREC_F32X2 && precision != SMASH_PREC_F32)
+    if (precision < SMASH_PREC_F64 || precision > SMASH_PREC_TF32X3)
         fail(SMASH_EINVAL, "unknown precision %d", precision);
     if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
         fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
@@ -350,8 +350,8 @@ void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int pre
                 Profile *prof) {
     if (precision == SMASH_PREC_F32X2)
         matvec_dd(h, X, Y, nrhs, s, prof);
-    else if (precision == SMASH_PREC_F32)
-        matvec_f32(h, X, Y, nrhs, s, prof);
+    else if (precision >= SMASH_PREC_F32)
+        matvec_f32(h, X, Y, nrhs, s, prof, precision);
     else
         matvec_f64(h, X, Y, nrhs, s, prof);
 }

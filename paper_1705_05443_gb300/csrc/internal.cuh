@@ -178,7 +178,12 @@ void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs,
 void matvec_dd(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
 bool dd_supported(int kernel_id);
 // mixed-precision matvec: FP32 kernel sums (Kahan-compensated near field), FP64 transfers
-void matvec_f32(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
+// (precision SMASH_PREC_F32, or SMASH_PREC_TF32/BF16/TF32X3 for tensor-core coupling products)
+void matvec_f32(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof,
+                int precision);
+// tensor-core coupling over L: FP32 entries of the normalised two-float coordinates
+// times q^ (FP32, ldq per slot) in TF32/BF16/split TF32, written to zhat (FP64) x scale
+void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s);
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "kappa_f32.cuh"
 #include "ksum_tiles.cuh"
 
 namespace smash {
@@ -35,6 +36,7 @@ struct KsumF32Args {
     double *out;       // target vectors (FP64), ldq
     double scale;      // multiplies the sums (1/s for 1/r and 1/(x-y), else 1)
     float s_f;         // s, for the Yukawa kernel
+    float inv_s;       // 1/s, for the Yukawa kernel
     float log_s;       // log s, for the log kernel
     int ldq, nchunks, tbp;
     int tile;          // source points staged per round (<= kF32Tile)
@@ -42,21 +44,6 @@ struct KsumF32Args {
 
 constexpr int kF32Threads = 256;
 constexpr int kF32Tile = 256;
-
-// kernel entry from the FP32 difference d (normalised units)
-template <int KID, int D>
-__device__ __forceinline__ float kappa_f32(const float *d, float s_f, float log_s) {
-    if (KID == SMASH_K_CAUCHY1D) return d[0] != 0.f ? __frcp_rn(d[0]) : 0.f;
-    float r2 = d[0] * d[0];
-    if (D > 1) r2 = fmaf(d[1], d[1], r2);
-    if (D > 2) r2 = fmaf(d[2], d[2], r2);
-    if (r2 == 0.f) return 0.f;
-    if (KID == SMASH_K_INVR) return rsqrtf(r2);
-    if (KID == SMASH_K_LOG) return fmaf(0.5f, __logf(r2), log_s);
-    float ri = rsqrtf(r2);
-    float r = r2 * ri * s_f;
-    return __expf(-r) * (ri / s_f);  // SMASH_K_YUKAWA
-}
 
 // One thread: TA targets x RC right-hand sides; the right-hand sides of a
 // source are read from shared memory as float4 (RC >= 4) and reused by the
@@ -137,7 +124,7 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
                     for (int u = 0; u < TA; ++u) {
                         float d[3] = {(xh[u].x - yh.x) + (xl[u].x - yl.x), (xh[u].y - yh.y) + (xl[u].y - yl.y),
                                       (xh[u].z - yh.z) + (xl[u].z - yl.z)};
-                        kv[u] = have[u] ? kappa_f32<KID, D>(d, a.s_f, a.log_s) : 0.f;
+                        kv[u] = have[u] ? kappa_f32<KID, D>(d, a.s_f, a.inv_s, a.log_s) : 0.f;
                     }
                     const float *qb = sq + (size_t)b * ldq + ch * RC;
                     constexpr int VW = RC >= 4 ? 4 : 1;  // vector width of the loads
@@ -243,6 +230,7 @@ static void ksum_f32(const smash_h2 *h, bool kahan, KsumF32Args a, int64_t ntn, 
     const bool mult = h->kernel_id == SMASH_K_INVR || h->kernel_id == SMASH_K_CAUCHY1D;
     a.scale = mult ? 1.0 / h->s : 1.0;
     a.s_f = (float)h->s;
+    a.inv_s = (float)(1.0 / h->s);
     a.log_s = (float)log(h->s);
     // tuned shape: bit 0 halves the source tile, bit 1 halves the target block cap
     std::vector<int> cands = {0, 1};
@@ -273,7 +261,8 @@ static void to_f32(const double *in, int64_t n, float *out, cudaStream_t s) {
     LAUNCHED();
 }
 
-void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof) {
+void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof,
+                int precision) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
     int ldq, RC;
@@ -308,7 +297,9 @@ void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
     matvec_upward(h, qs, qhat, ldq, s);
     to_f32(qhat, Cs.total_skel * ldq, qhat1, s);
     tm.mark();
-    if (h->nnodes > h->nroots) {
+    if (h->nnodes > h->nroots && precision != SMASH_PREC_F32) {
+        coupling_tc(h, precision, qhat1, zhat, ldq, s);
+    } else if (h->nnodes > h->nroots) {
         KsumF32Args a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;

@@ -168,7 +168,7 @@ smash_status smash_server_create(int max_inflight, size_t mem_budget_bytes, int 
     if (!out) return server_fail(SMASH_EINVAL, "out is NULL");
     *out = nullptr;
     if (max_inflight < 1 || max_inflight > 64) return server_fail(SMASH_EINVAL, "max_inflight must be in [1, 64]");
-    if (precision < SMASH_PREC_F64 || precision > SMASH_PREC_F32) return server_fail(SMASH_EINVAL, "bad precision");
+    if (precision < SMASH_PREC_F64 || precision > SMASH_PREC_TF32X3) return server_fail(SMASH_EINVAL, "bad precision");
     auto *s = new smash_server();
     s->max_inflight = max_inflight;
     s->precision = precision;
