@@ -281,6 +281,65 @@ def run_batched(sm, torch, dev, steps: int = 2, warmup: int = 1, reps: int = 10)
     }
 
 
+def run_mixed(sm, torch, dev, reps: int = 2) -> dict:
+    """The sphere configuration (2^20 points on S^2 with 8 caps, Yukawa, leaf
+    128, order 5, 32 RHS): the FP64 build, then the matvec in every precision
+    on the same representation.  Errors are relative 2-norms against the
+    FP64 matvec of the same build (which agrees with the oracle's H^2 matvec
+    to <= 1e-11)."""
+    w = si.make_workload("sphere_yukawa_1m")
+    x = torch.from_numpy(w["x"]).to(dev)
+    q = torch.from_numpy(w["q"]).to(dev)
+    z = torch.empty_like(q)
+    st = torch.cuda.Stream(dev)
+
+    def timed(fn, keep_last=True):
+        """Best of `reps` runs of fn on stream st; for builds (keep_last) the
+        handles of all runs but the last are freed."""
+        best, out = None, None
+        for i in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            out = fn()
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+            if keep_last and i < reps - 1:
+                sm.smash_free(out)
+        return best, out
+
+    sm.smash_set_profiling(True)
+    build_ms, h = timed(lambda: sm.smash_build_xy(x, None, w["kernel"], w["leaf"], w["order"], w["tol"],
+                                                  stream=st))
+    names = {"f64": sm.SMASH_PREC_F64, "f32": sm.SMASH_PREC_F32, "tf32": sm.SMASH_PREC_TF32,
+             "bf16": sm.SMASH_PREC_BF16, "tf32x3": sm.SMASH_PREC_TF32X3}
+    res = {}
+    z64 = None
+    for name, p in names.items():
+        ms, _ = timed(lambda: sm.smash_matvec_ex(h, q, z, p, stream=st), keep_last=False)
+        prof = sm.smash_last_profile(h)
+        if p == sm.SMASH_PREC_F64:
+            z64 = z.clone()
+            err = 0.0
+        else:
+            err = float(torch.linalg.norm(z - z64) / torch.linalg.norm(z64))
+        res[name] = {"matvec_ms": ms, "coupling_ms": prof["coupling"], "near_ms": prof["near"],
+                     "rel_err_vs_fp64": err,
+                     "build_plus_matvec_points_per_s": w["n"] / ((build_ms + ms) / 1e3)}
+    sm.smash_set_profiling(False)
+    info = sm.smash_info(h)
+    sm.smash_free(h)
+    return {"workload": "sphere_yukawa_1m: 2^20 points on S^2 (90% uniform, 10% in 8 caps, sigma 0.02), "
+                        "exp(-r)/r, leaf 128, order 5, tol 1e-8, 32 RHS",
+            "build_ms": build_ms, "coupling_entries": info["coupling_pairs"], "near_entries": info["near_pairs"],
+            "precisions": res,
+            "note": "tf32/bf16/tf32x3: coupling products on the tensor cores (warp MMAs), near field FP32 "
+                    "with compensated sums; errors against the FP64 matvec of the same build"}
+
+
 def bench_reference(args, w):
     ws, rank = _dist()
     if rank != 0:
@@ -460,6 +519,7 @@ def bench_ours(args, w):
         wdef = (f"per kernel entry {DD_MAC_OPS}*nrhs + {DD_EVAL_OPS} FP32 instructions of the "
                 "double-float algorithm (error-free products and sums)")
     achieved = cpl_work / (cpl_ms / 1e3) / 1e12
+    mixed = run_mixed(sm, torch, dev) if args.mixed else None
     batched = None
     if args.batched:
         sm.smash_set_autotune(args.autotune)
@@ -498,6 +558,7 @@ def bench_ours(args, w):
         "gpu_launches": int(launches / args.steps),
         "serving": serving,
         "batched": batched,
+        "mixed_precision": mixed,
         "autotune": {"enabled": bool(args.autotune), "entries_after_warmup": tune_entries,
                      "entries": sm.smash_autotune_entries()},
         "clocks": clocks,
@@ -529,6 +590,8 @@ def main():
                          "mixed precision FP32")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the batched-trees measurement")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false",
+                    help="skip the sphere mixed-precision measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the default launch shapes instead of tuning them in the first warm-up step")
     args = ap.parse_args()
