@@ -212,22 +212,24 @@ struct KsumDDArgs {
     double *out;       // target vectors (FP64), ldq
     double scale;      // 1/s
     int ldq, nchunks, tbp, groups;
-    int tile;          // source points staged per round (<= kDdTile)
+    int tile;          // source points staged per round (at least; <= tile_cap)
+    int tile_cap;      // shared-memory capacity in sources (the layout's stride)
 };
 
 constexpr int kDdThreads = 256;
 constexpr int kDdTile = 128;
+constexpr int kDdTileMax = 256;
 
 template <int KID, int D, int RC, bool EXACT>
 __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
     constexpr int NC = EXACT ? 3 : 2;                                 // float4 per point
-    const int tile = a.tile;                                         // <= kDdTile
-    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // tile * NC
-    float2 *sq = reinterpret_cast<float2 *>(sy + NC * tile);         // tile * ldq
-    double *red = reinterpret_cast<double *>(sq + (size_t)tile * a.ldq);  // tbp * ldq
-    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);
+    const int cap = a.tile_cap;
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // cap * NC
+    float2 *sq = reinterpret_cast<float2 *>(sy + NC * cap);          // cap * ldq
+    double *red = reinterpret_cast<double *>(sq + (size_t)cap * a.ldq);  // tbp * ldq
+    int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);  // cap
 
     const int64_t g = a.tnodes[blockIdx.x];
     const int T = a.t_cnt[g];
@@ -247,6 +249,9 @@ __global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
     const int ta = lt % tbp;
     const int ch = lt / tbp;
     const bool active = grp < groups;
+    // sources per round: at least a.tile, and enough that each source group
+    // takes 32 of them between two barriers (small target blocks have many groups)
+    const int tile = max(a.tile, min(cap, 32 * groups));
 
     for (int tb = 0; tb < T; tb += tbp) {
         const int tcount = min(tbp, T - tb);
@@ -345,8 +350,13 @@ template <int KID, int D, bool EXACT>
 static void launch_dd(KsumDDArgs a, int64_t ntn, int RC, cudaStream_t s) {
     if (ntn <= 0) return;
     constexpr int NC = EXACT ? 3 : 2;
-    size_t smem = sizeof(float4) * NC * a.tile + sizeof(float2) * (size_t)a.tile * a.ldq +
-                  sizeof(double) * (size_t)a.tbp * a.ldq + sizeof(int64_t) * a.tile;
+    auto bytes = [&](int cap) {
+        return sizeof(float4) * NC * cap + sizeof(float2) * (size_t)cap * a.ldq + sizeof(double) * (size_t)a.tbp * a.ldq +
+               sizeof(int64_t) * cap;
+    };
+    // room for the larger rounds of small target blocks while two CTAs fit per SM
+    a.tile_cap = bytes(kDdTileMax) <= 96 * 1024 ? std::max(a.tile, kDdTileMax) : a.tile;
+    size_t smem = bytes(a.tile_cap);
     void (*kern)(KsumDDArgs) = nullptr;
     switch (RC) {
     case 1: kern = ksum_dd_kernel<KID, D, 1, EXACT>; break;
