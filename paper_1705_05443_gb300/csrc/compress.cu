@@ -46,8 +46,10 @@ struct CompressArgs {
     int32_t *nswaps;
     double *work;             // per-CTA slots of slot_doubles
     int64_t slot_doubles;
+    int64_t x_off;            // R11^{-1} (r x r) at this offset in a slot
     int m_cap;
-    int w_in_smem;
+    int64_t w_smem_doubles;   // W region in shared memory (0: none); a node with
+                              // r m above it keeps W in its global slot
 };
 
 // ---------------------------------------------------------------- setup
@@ -314,8 +316,8 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
         sh.rval = dp; dp += NT / 32;
         sh.ctrl = dp; dp += 8;
         sh.ridx = reinterpret_cast<int64_t *>(dp); dp += NT / 32;
-        sh.W = a.w_in_smem ? dp : nullptr;
-        if (a.w_in_smem) dp += (int64_t)a.r * a.m_cap;
+        sh.W = a.w_smem_doubles ? dp : nullptr;
+        dp += a.w_smem_doubles;
         int *ip = reinterpret_cast<int *>(dp);
         sh.perm = ip; ip += a.m_cap;
         sh.ex = ip; ip += a.m_cap;
@@ -323,8 +325,7 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
     }
     const int tid = threadIdx.x;
     double *slot = a.work + (int64_t)blockIdx.x * a.slot_doubles;
-    double *W = a.w_in_smem ? sh.W : slot;
-    double *X = slot + (a.w_in_smem ? 0 : (int64_t)a.r * a.m_cap);  // R11^{-1}, k x k
+    double *X = slot + a.x_off;  // R11^{-1}, k x k
     const int r = a.r;
 
     for (int64_t ni = blockIdx.x; ni < a.nl; ni += gridDim.x) {
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
             continue;
         }
         const int ld = m;
+        double *W = (int64_t)r * m <= a.w_smem_doubles ? sh.W : slot;
         // 1. W = U^^T
         for (int c = tid; c < m; c += NT) {
             basis_column<PMAX>(a, g, working_gid(a, g, c), W, ld, c);
@@ -561,20 +563,42 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         // (each column is reduced by one thread in the oracle's order).  The
         // default gives one column per thread up to 512 threads.
         const bool small_p = h->order <= 16;
+        // W stays in shared memory up to the opt-in limit of one CTA (less a
+        // margin); larger working sets use a global slot in the L2
+        int optin = 0;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+        const size_t w_smem_limit = (size_t)std::max(0, optin - 2048);
         struct Plan {
             void (*kern)(CompressArgs);
             size_t smem;
             int64_t grid;
-            bool w_in_smem;
-            int64_t slot_doubles;
+            bool all_in_smem;
+            int64_t w_smem_doubles, slot_doubles, x_off;
         };
-        auto plan = [&](int NT, Plan &pl) -> bool {
+        // a candidate is NT + kCpsUnit * c: NT threads per CTA and, for levels
+        // whose largest W does not fit, a W region of 1/c of the opt-in limit
+        // (c CTAs per SM, so that one CTA's serial phases overlap another's
+        // column updates)
+        constexpr int kCpsUnit = 4096;
+        auto plan = [&](int cand, Plan &pl) -> bool {
+            const int NT = cand % kCpsUnit, cps = std::max(1, cand / kCpsUnit);
             size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
                                sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
             size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
-            pl.w_in_smem = (base_smem + w_bytes) <= 160 * 1024;
-            pl.smem = base_smem + (pl.w_in_smem ? w_bytes : 0);
-            pl.slot_doubles = (pl.w_in_smem ? 0 : (int64_t)h->r * m_cap) + (int64_t)h->r * h->r;
+            pl.all_in_smem = (base_smem + w_bytes) <= w_smem_limit;
+            if (pl.all_in_smem) {
+                pl.w_smem_doubles = (int64_t)h->r * m_cap;
+                pl.x_off = 0;
+            } else {
+                // as much of W as fits in 1/cps of the limit; the nodes above it use
+                // the global slot
+                const size_t lim = w_smem_limit / cps;
+                int64_t room = base_smem < lim ? (int64_t)((lim - base_smem) / sizeof(double)) : 0;
+                pl.w_smem_doubles = room >= h->r ? room : 0;
+                pl.x_off = (int64_t)h->r * m_cap;
+            }
+            pl.smem = base_smem + sizeof(double) * (size_t)pl.w_smem_doubles;
+            pl.slot_doubles = pl.x_off + (int64_t)h->r * h->r;
             if (NT == 64) pl.kern = small_p ? compress_kernel<64, 16> : compress_kernel<64, kMaxP>;
             else if (NT == 128) pl.kern = small_p ? compress_kernel<128, 16> : compress_kernel<128, kMaxP>;
             else if (NT == 256) pl.kern = small_p ? compress_kernel<256, 16> : compress_kernel<256, kMaxP>;
@@ -585,7 +609,7 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
             if (per_sm < 1) return false;
             pl.grid = std::min<int64_t>(nl, (int64_t)per_sm * h->num_sms);
             // keep the concurrent node matrices of a global-slot level inside the L2
-            if (!pl.w_in_smem) {
+            if (!pl.all_in_smem) {
                 int64_t fit = (int64_t)(64ll << 20) / (pl.slot_doubles * (int64_t)sizeof(double));
                 pl.grid = std::max<int64_t>(1, std::min<int64_t>(pl.grid, std::max<int64_t>(fit, h->num_sms)));
             }
@@ -597,14 +621,22 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
         if (!plan(NT_def, pdef)) fail(SMASH_ENOTSUP, "compression kernel does not fit on an SM (%zu B smem)", pdef.smem);
         for (int nt = 64; nt <= 512; nt *= 2) {
             Plan pl;
-            if (plan(nt, pl)) cands.push_back(nt);
+            if (!plan(nt, pl)) continue;
+            cands.push_back(nt);
+            if (!pl.all_in_smem)
+                for (int cps = 2; cps <= 4; cps *= 2) {
+                    Plan p2;
+                    if (plan(nt + kCpsUnit * cps, p2)) cands.push_back(nt + kCpsUnit * cps);
+                }
         }
-        auto run = [&](int NT) {
+        auto run = [&](int cand) {
+            const int NT = cand % kCpsUnit;
             Plan pl;
-            plan(NT, pl);
+            plan(cand, pl);
             CompressArgs b = a;
-            b.w_in_smem = pl.w_in_smem;
+            b.w_smem_doubles = pl.w_smem_doubles;
             b.slot_doubles = pl.slot_doubles;
+            b.x_off = pl.x_off;
             int64_t need = pl.grid * pl.slot_doubles;
             if (need > work_cap) {
                 if (work) scratch.free(work);
