@@ -163,6 +163,23 @@ SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *
                              void *stream);
 
 /*
+ * smash_matvec_cauchy_like -- Y = A X for the Cauchy-like matrix of (6.1):
+ * a_ij = kappa(x_i, y_j) sum_{l<p} w_il v_jl, i.e. (6.2)
+ * A = sum_l diag(w_l) C diag(v_l) with C the matrix that h approximates
+ * (Section 6.3 takes kappa = 1/(x - y), SMASH_K_CAUCHY1D; any kernel works).
+ * The p scaled copies of X run through the H^2 matvec as one block of
+ * p * nrhs right-hand sides and are recombined row by row in the order of l.
+ *   w  nx x p float64, row-major (host or device);  v  ny x p likewise
+ *   X  ny x nrhs, Y  nx x nrhs (caller point order), as smash_matvec_ex
+ *   precision, stream: as smash_matvec_ex
+ * Errors: SMASH_EINVAL (NULL pointers, p < 1, p * nrhs outside [1, 64],
+ * the errors of smash_matvec_ex), SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_matvec_cauchy_like(smash_handle h, const double *w, const double *v, int p,
+                                                const double *X, double *Y, int nrhs, int precision,
+                                                void *stream);
+
+/*
  * smash_matvec_noalloc -- the FP64 matvec of smash_matvec_ex that allocates
  * no device memory, for callers that cannot allocate while they run (a host
  * that gives all free device memory to its own pool allocator up front, or a

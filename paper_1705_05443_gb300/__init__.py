@@ -21,7 +21,7 @@ from . import _build
 
 __all__ = [
     "SmashError", "smash_build", "smash_build_xy", "smash_build_batch", "smash_matvec", "smash_matvec_ex",
-    "smash_matvec_graph", "smash_matvec_graph_count", "smash_set_autotune", "smash_autotune_load",
+    "smash_matvec_graph", "smash_matvec_graph_count", "smash_matvec_cauchy_like", "smash_set_autotune", "smash_autotune_load",
     "smash_autotune_save", "smash_autotune_entries", "smash_autotune_clear", "smash_autotune_lookup",
     "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
@@ -103,6 +103,8 @@ def load_library(build: bool = True):
     lib.smash_build_xy.restype = i32
     lib.smash_build_batch.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
     lib.smash_build_batch.restype = i32
+    lib.smash_matvec_cauchy_like.argtypes = [P, P, P, i32, P, P, i32, i32, P]
+    lib.smash_matvec_cauchy_like.restype = i32
     lib.smash_matvec_graph.argtypes = [P, P, P, i32, i32, P]
     lib.smash_matvec_graph.restype = i32
     lib.smash_matvec_graph_count.argtypes = [P]
@@ -253,6 +255,15 @@ def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
     _check(lib.smash_matvec_noalloc(h, _ptr(X), _ptr(Y), nrhs, _stream_ptr(stream)))
+    return Y
+
+
+def smash_matvec_cauchy_like(h, w, v, X, Y, precision: int = SMASH_PREC_F64, stream=None):
+    """Y = sum_l diag(w[:, l]) C^ diag(v[:, l]) X, the Cauchy-like product (6.1)-(6.2)."""
+    lib = load_library()
+    p = int(w.shape[1])
+    _check(lib.smash_matvec_cauchy_like(h, _ptr(w), _ptr(v), p, _ptr(X), _ptr(Y), int(X.shape[1]), precision,
+                                        _stream_ptr(stream)))
     return Y
 
 

@@ -22,6 +22,7 @@ __all__ = [
     "gaussian_mixture",
     "cauchy_1d",
     "jittered_grid",
+    "cauchy_like_6_3",
     "rhs",
     "sample_rows",
     "batched_problems",
@@ -79,6 +80,18 @@ def cauchy_1d(n: int, seed: int, offset: float = 1e-3):
     y = x + offset * g.random((n, 1))
     return (np.ascontiguousarray(x, dtype=np.float64),
             np.ascontiguousarray(y, dtype=np.float64))
+
+
+def cauchy_like_6_3(n: int, seed: int, offset: float = 1e-7, p: int = 2):
+    """The first point sets of Section 6.3, (6.3): x_k = k/(n+1) and
+    y_k = x_k + offset U(0,1), with generators w, v (n x p) of U(0,1) entries
+    as the paper draws them.  Returns (x, y, w, v); x, y of shape (n, 1)."""
+    g = _rng(seed)
+    x = (np.arange(1, n + 1, dtype=np.float64) / (n + 1))[:, None]
+    y = x + offset * g.random((n, 1))
+    w = g.random((n, p))
+    v = g.random((n, p))
+    return tuple(np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, w, v))
 
 
 def jittered_grid(cells_per_dim: int, d: int, seed: int, per_cell: int = 1) -> np.ndarray:

@@ -153,3 +153,9 @@ def test_matvec_graph_rejects_null_handle():
     assert lib.smash_matvec_graph(None, None, None, 1, 0, None) == 1
     assert "NULL" in lib.smash_last_error().decode()
     assert lib.smash_matvec_graph_count(None) == 0
+
+
+def test_cauchy_like_rejects_bad_arguments_without_a_device():
+    lib = sm.load_library()
+    assert lib.smash_matvec_cauchy_like(None, None, None, 2, None, None, 1, 0, None) == 1
+    assert "NULL" in lib.smash_last_error().decode()
