@@ -58,7 +58,13 @@ enum {
     SMASH_K_LOG = 0,     /* log |x - y|                 */
     SMASH_K_INVR = 1,    /* 1 / |x - y|                 */
     SMASH_K_YUKAWA = 2,  /* exp(-|x - y|) / |x - y|     */
-    SMASH_K_CAUCHY1D = 3 /* 1 / (x - y), dim = 1, (6.1) */
+    SMASH_K_CAUCHY1D = 3, /* 1 / (x - y), dim = 1, (6.1) */
+    /* The y-gradient of the fundamental solution Phi = -(1/2 pi) log|x - y| of
+     * Section 6.4, component by component (dim = 2):
+     * -(1/2 pi) (y_a - x_a) / |x - y|^2, 0 at coincident points.  The double-layer
+     * kernel (6.9) is sum_a of these times nu_a(y) |r'(t)| (smash_matvec_double_layer). */
+    SMASH_K_DLP1 = 4,
+    SMASH_K_DLP2 = 5
 };
 
 /* Arithmetic of the matvec (Section 3.4).  The build is always FP64. */
@@ -161,6 +167,39 @@ SMASH_API smash_status smash_matvec(smash_handle h, const double *X, double *Y, 
  */
 SMASH_API smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision,
                              void *stream);
+
+/*
+ * smash_matvec_kernel -- smash_matvec_ex with another kernel on the same
+ * representation.  The bases and generators of Section 3 depend only on the
+ * points and the cells (the interpolation basis (2.2) and its compression),
+ * not on kappa; only the coupling (3.19) and near-field (3.20) entries do.
+ * So one build serves every kernel valid for its dimension.
+ *   kernel_id  SMASH_K_*, valid for the handle's dim
+ * Errors: as smash_matvec_ex; SMASH_EINVAL for a kernel the dimension does
+ * not allow, and for SMASH_PREC_F32X2 on a handle built for a kernel other
+ * than 1/|x-y| or 1/(x-y).
+ */
+SMASH_API smash_status smash_matvec_kernel(smash_handle h, int kernel_id, const double *X, double *Y, int nrhs,
+                                           int precision, void *stream);
+
+/*
+ * smash_matvec_double_layer -- Y = K X for the Nystrom discretisation of the
+ * double-layer operator (6.7) with kernel (6.9) on the points of h (X = Y,
+ * dim = 2): K_ij = grad_y Phi(x_i, x_j) . nu_j w_j for i != j, K_ii = diag_i,
+ * with Phi = -(1/2 pi) log|x - y|.  Evaluated as
+ * K X = A_1 diag(nu_1 w) X + A_2 diag(nu_2 w) X + diag(diag) X, where A_a is
+ * the H^2 matrix of SMASH_K_DLP1/2 on the same representation.
+ *   nu    n x 2 unit normals at the points (row-major), w  n quadrature
+ *         weights (|r'(t_j)| h for the trapezoidal rule), diag  n diagonal
+ *         entries (the kernel's limit at coincident points) or NULL for 0;
+ *         host or device memory
+ *   X, Y  n x nrhs, precision and stream as smash_matvec_ex (not F32X2)
+ * Errors: SMASH_EINVAL (NULL normals or weights, dim != 2, nx != ny, the
+ * errors of smash_matvec_ex), SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_matvec_double_layer(smash_handle h, const double *nu, const double *wts,
+                                                 const double *diag, const double *X, double *Y, int nrhs,
+                                                 int precision, void *stream);
 
 /*
  * smash_matvec_cauchy_like -- Y = A X for the Cauchy-like matrix of (6.1):

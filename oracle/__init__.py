@@ -35,6 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 KERNEL_LOG, KERNEL_INVR, KERNEL_YUKAWA, KERNEL_CAUCHY = 0, 1, 2, 3
+KERNEL_DLP1, KERNEL_DLP2 = 4, 5  # y-gradient of -(1/2 pi) log|x - y| (Section 6.4), d = 2
 
 _Q = dict(nx=0, ny=1, L=2, nnodes=3, nadm=4, nnear=5, same=6, skel_row=7, rest_row=8,
           g_row=9, skel_col=10, rest_col=11, g_col=12, r=13, swaps_row=14, swaps_col=15,

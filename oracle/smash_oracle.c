@@ -40,7 +40,7 @@
 #define ORC_MAXP 64
 #define ORC_MAX_SWAPS 1000
 
-enum { ORC_K_LOG = 0, ORC_K_INVR = 1, ORC_K_YUKAWA = 2, ORC_K_CAUCHY = 3 };
+enum { ORC_K_LOG = 0, ORC_K_INVR = 1, ORC_K_YUKAWA = 2, ORC_K_CAUCHY = 3, ORC_K_DLP1 = 4, ORC_K_DLP2 = 5 };
 
 /* ------------------------------------------------------------------------ */
 /* kernels (2.1) with the diagonal value 0                                   */
@@ -59,6 +59,10 @@ double orc_kernel(int kid, int d, const double *x, const double *y)
     }
     if (r2 == 0.0)
         return 0.0;
+    /* Section 6.4: the gradient in y of Phi(x, y) = -(1/2 pi) log|x - y| is
+     * -(1/2 pi) (y - x) / |x - y|^2; kernels 4 and 5 are its two components (d = 2) */
+    if (kid == ORC_K_DLP1) return -(y[0] - x[0]) / (2.0 * ORC_PI * r2);
+    if (kid == ORC_K_DLP2) return -(y[1] - x[1]) / (2.0 * ORC_PI * r2);
     double r = sqrt(r2);
     switch (kid) {
     case ORC_K_LOG: return log(r);
@@ -689,7 +693,8 @@ orc_h2 *orc_build(const double *x, int64_t nx, const double *y, int64_t ny, int 
     if (d < 1 || d > 3 || nx < 1 || leaf < 1 || p < 1 || p > ORC_MAXP || !(tol > 0.0) ||
         !(tau > 0.0 && tau < 1.0) || !(f > 1.0))
         return NULL;
-    if (kid < 0 || kid > 3 || (kid == ORC_K_CAUCHY && d != 1)) return NULL;
+    if (kid < 0 || kid > 5 || (kid == ORC_K_CAUCHY && d != 1) || ((kid == ORC_K_DLP1 || kid == ORC_K_DLP2) && d != 2))
+        return NULL;
     if (y && ny < 1) return NULL;
     for (int64_t i = 0; i < nx * d; ++i) if (!isfinite(x[i])) return NULL;
     if (y) for (int64_t i = 0; i < ny * d; ++i) if (!isfinite(y[i])) return NULL;

@@ -21,7 +21,8 @@ from . import _build
 
 __all__ = [
     "SmashError", "smash_build", "smash_build_xy", "smash_build_batch", "smash_matvec", "smash_matvec_ex",
-    "smash_matvec_graph", "smash_matvec_graph_count", "smash_matvec_cauchy_like", "smash_set_autotune", "smash_autotune_load",
+    "smash_matvec_graph", "smash_matvec_graph_count", "smash_matvec_cauchy_like", "smash_matvec_kernel",
+    "smash_matvec_double_layer", "SMASH_K_DLP1", "SMASH_K_DLP2", "smash_set_autotune", "smash_autotune_load",
     "smash_autotune_save", "smash_autotune_entries", "smash_autotune_clear", "smash_autotune_lookup",
     "smash_matvec_noalloc", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
@@ -33,6 +34,7 @@ __all__ = [
 ]
 
 SMASH_K_LOG, SMASH_K_INVR, SMASH_K_YUKAWA, SMASH_K_CAUCHY1D = 0, 1, 2, 3
+SMASH_K_DLP1, SMASH_K_DLP2 = 4, 5
 SMASH_PREC_F64 = 0
 SMASH_PREC_F32X2 = 1
 SMASH_PREC_F32 = 2
@@ -103,6 +105,10 @@ def load_library(build: bool = True):
     lib.smash_build_xy.restype = i32
     lib.smash_build_batch.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
     lib.smash_build_batch.restype = i32
+    lib.smash_matvec_kernel.argtypes = [P, i32, P, P, i32, i32, P]
+    lib.smash_matvec_kernel.restype = i32
+    lib.smash_matvec_double_layer.argtypes = [P, P, P, P, P, P, i32, i32, P]
+    lib.smash_matvec_double_layer.restype = i32
     lib.smash_matvec_cauchy_like.argtypes = [P, P, P, i32, P, P, i32, i32, P]
     lib.smash_matvec_cauchy_like.restype = i32
     lib.smash_matvec_graph.argtypes = [P, P, P, i32, i32, P]
@@ -255,6 +261,21 @@ def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
     _check(lib.smash_matvec_noalloc(h, _ptr(X), _ptr(Y), nrhs, _stream_ptr(stream)))
+    return Y
+
+
+def smash_matvec_kernel(h, kernel_id: int, X, Y, precision: int = SMASH_PREC_F64, stream=None):
+    """Y = A^_kappa X with another kernel on the same representation (see smash.h)."""
+    lib = load_library()
+    _check(lib.smash_matvec_kernel(h, kernel_id, _ptr(X), _ptr(Y), int(X.shape[1]), precision, _stream_ptr(stream)))
+    return Y
+
+
+def smash_matvec_double_layer(h, nu, wts, diag, X, Y, precision: int = SMASH_PREC_F64, stream=None):
+    """Y = K X, the Nystrom double-layer matrix (6.7)/(6.9) on the handle's points (see smash.h)."""
+    lib = load_library()
+    _check(lib.smash_matvec_double_layer(h, _ptr(nu), _ptr(wts), _ptr(diag), _ptr(X), _ptr(Y), int(X.shape[1]),
+                                         precision, _stream_ptr(stream)))
     return Y
 
 

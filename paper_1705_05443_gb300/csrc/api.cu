@@ -197,8 +197,7 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
         for (int a = 0; a < dim; ++a) r *= order;
         if (r > kMaxR) fail(SMASH_EINVAL, "order^dim = %d exceeds %d", r, kMaxR);
         if (!(tol > 0.0) || !std::isfinite(tol)) fail(SMASH_EINVAL, "tol must be positive and finite");
-        if (kernel_id < 0 || kernel_id > 3) fail(SMASH_EINVAL, "unknown kernel_id %d", kernel_id);
-        if (kernel_id == SMASH_K_CAUCHY1D && dim != 1) fail(SMASH_EINVAL, "the Cauchy kernel needs dim == 1");
+        check_kernel(kernel_id, dim);
         if (!(o.tau > 0.0 && o.tau < 1.0)) fail(SMASH_EINVAL, "tau must be in (0, 1)");
         if (!(o.f > 1.0)) fail(SMASH_EINVAL, "f must be > 1");
 
@@ -336,33 +335,46 @@ smash_status smash_build_batch(const double *points, const int64_t *offsets, int
 
 namespace smash {
 
-void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision) {
+void check_kernel(int kernel_id, int dim) {
+    if (kernel_id < 0 || kernel_id > SMASH_K_DLP2) fail(SMASH_EINVAL, "unknown kernel_id %d", kernel_id);
+    if (kernel_id == SMASH_K_CAUCHY1D && dim != 1) fail(SMASH_EINVAL, "the Cauchy kernel needs dim == 1");
+    if ((kernel_id == SMASH_K_DLP1 || kernel_id == SMASH_K_DLP2) && dim != 2)
+        fail(SMASH_EINVAL, "the double-layer kernels need dim == 2");
+}
+
+void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision, int kid) {
     if (!h) fail(SMASH_EINVAL, "handle is NULL");
+    if (kid < 0) kid = h->kernel_id;
+    check_kernel(kid, h->dim);
     if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
     if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
     if (precision < SMASH_PREC_F64 || precision > SMASH_PREC_TF32X3)
         fail(SMASH_EINVAL, "unknown precision %d", precision);
-    if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
+    if (precision == SMASH_PREC_F32X2 && !dd_supported(kid))
         fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
+    if (precision == SMASH_PREC_F32X2 && !h->xs_x3)
+        fail(SMASH_EINVAL, "SMASH_PREC_F32X2 needs a handle built for 1/|x-y| or 1/(x-y)");
 }
 
 void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int precision, cudaStream_t s,
-                Profile *prof) {
+                Profile *prof, int kid) {
+    if (kid < 0) kid = h->kernel_id;
     if (precision == SMASH_PREC_F32X2)
-        matvec_dd(h, X, Y, nrhs, s, prof);
+        matvec_dd(h, X, Y, nrhs, s, prof, kid);
     else if (precision >= SMASH_PREC_F32)
-        matvec_f32(h, X, Y, nrhs, s, prof, precision);
+        matvec_f32(h, X, Y, nrhs, s, prof, precision, kid);
     else
-        matvec_f64(h, X, Y, nrhs, s, prof);
+        matvec_f64(h, X, Y, nrhs, s, prof, kid);
 }
 
 }  // namespace smash
 
 extern "C" {
 
-smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision, void *stream) {
+static smash_status matvec_impl(smash_handle h, int kid, const double *X, double *Y, int nrhs, int precision,
+                                void *stream) {
     try {
-        check_matvec_args(h, X, Y, nrhs, precision);
+        check_matvec_args(h, X, Y, nrhs, precision, kid);
         cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
         Arena io(s);
         const double *Xd = X;
@@ -375,7 +387,7 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         }
         if (yhost) Yd = io.alloc<double>((size_t)h->nx * nrhs);
         h->prof_mv.on = profiling_enabled();
-        run_matvec(h, Xd, Yd, nrhs, precision, s, &h->prof_mv);
+        run_matvec(h, Xd, Yd, nrhs, precision, s, &h->prof_mv, kid);
         if (yhost) CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         io.release();
         if (yhost || !stream) CK(cudaStreamSynchronize(s));
@@ -386,6 +398,19 @@ smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrh
         t_last_error = "host allocation failed";
         return SMASH_ENOMEM;
     }
+}
+
+smash_status smash_matvec_ex(smash_handle h, const double *X, double *Y, int nrhs, int precision, void *stream) {
+    return matvec_impl(h, -1, X, Y, nrhs, precision, stream);
+}
+
+smash_status smash_matvec_kernel(smash_handle h, int kernel_id, const double *X, double *Y, int nrhs, int precision,
+                                 void *stream) {
+    if (kernel_id < 0) {
+        t_last_error = "kernel_id must be >= 0";
+        return SMASH_EINVAL;
+    }
+    return matvec_impl(h, kernel_id, X, Y, nrhs, precision, stream);
 }
 
 smash_status smash_matvec(smash_handle h, const double *X, double *Y, int nrhs) {

@@ -173,17 +173,19 @@ void build_stats(smash_h2 *h, Arena &scratch);
 
 // matvec in FP64: X_dev (ny x nrhs), Y_dev (nx x nrhs), both device
 void matvec_f64(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
-                Profile *prof);
+                Profile *prof, int kid);
 // matvec with double-float kernel sums (kernels 1/|x-y| and 1/(x-y))
-void matvec_dd(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof);
+void matvec_dd(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof,
+               int kid);
 bool dd_supported(int kernel_id);
 // mixed-precision matvec: FP32 kernel sums (Kahan-compensated near field), FP64 transfers
 // (precision SMASH_PREC_F32, or SMASH_PREC_TF32/BF16/TF32X3 for tensor-core coupling products)
 void matvec_f32(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s, Profile *prof,
-                int precision);
+                int precision, int kid);
 // tensor-core coupling over L: FP32 entries of the normalised two-float coordinates
 // times q^ (FP32, ldq per slot) in TF32/BF16/split TF32, written to zhat (FP64) x scale
-void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s);
+void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s,
+                 int kid);
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);
@@ -208,9 +210,12 @@ bool profiling_enabled();
 
 // argument checks of the matvec entry points (fail() on bad input) and the
 // precision dispatch they share
-void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision);
+// (kid < 0: the kernel the handle was built for; the bases depend only on the
+// points and cells, so any kernel valid for the dimension applies)
+void check_kernel(int kernel_id, int dim);
+void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision, int kid = -1);
 void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int precision, cudaStream_t s,
-                Profile *prof);
+                Profile *prof, int kid = -1);
 void destroy_graphs(smash_h2 *h);
 
 // ---------------------------------------------------------------- autotuning

@@ -19,6 +19,9 @@ __device__ __forceinline__ double kappa64(double dx, double dy, double dz) {
     if (KID == SMASH_K_CAUCHY1D) return dx != 0.0 ? 1.0 / dx : 0.0;
     double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 == 0.0) return 0.0;
+    // y-gradient of -(1/2pi) log|x - y| with d = x - y: d_a / (2 pi |d|^2)
+    if (KID == SMASH_K_DLP1) return dx / (6.283185307179586 * r2);
+    if (KID == SMASH_K_DLP2) return dy / (6.283185307179586 * r2);
     if (KID == SMASH_K_INVR) return rsqrt(r2);
     if (KID == SMASH_K_LOG) return 0.5 * log(r2);
     double r = sqrt(r2);
@@ -239,6 +242,8 @@ static void ksum_launch(int kid, KsumArgs a, int64_t ntn, int RC, cudaStream_t s
     case SMASH_K_LOG: launch_ksum<SMASH_K_LOG>(a, ntn, RC, s); break;
     case SMASH_K_INVR: launch_ksum<SMASH_K_INVR>(a, ntn, RC, s); break;
     case SMASH_K_YUKAWA: launch_ksum<SMASH_K_YUKAWA>(a, ntn, RC, s); break;
+    case SMASH_K_DLP1: launch_ksum<SMASH_K_DLP1>(a, ntn, RC, s); break;
+    case SMASH_K_DLP2: launch_ksum<SMASH_K_DLP2>(a, ntn, RC, s); break;
     default: launch_ksum<SMASH_K_CAUCHY1D>(a, ntn, RC, s); break;
     }
 }
@@ -282,7 +287,7 @@ static void rhs_layout(int nrhs, int &ldq, int &RC) {
     }
 }
 
-void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof) {
+void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof, int kid) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
     int ldq, RC;
@@ -303,7 +308,7 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs; a.ys = h->ys; a.qv = qs; a.out = zs; a.ldq = ldq;
-        ksum(h, h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum(h, kid, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
     for (int l = h->L; l >= 2; --l) {
@@ -319,7 +324,7 @@ void matvec_f64(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_xyz; a.ys = Cs.skel_xyz; a.qv = qhat; a.out = zhat; a.ldq = ldq;
-        ksum(h, h->kernel_id, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum(h, kid, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     for (int l = 2; l <= h->L; ++l) {

@@ -386,9 +386,9 @@ static void ksum_dd_dispatch(int kid, int dim, KsumDDArgs a, int64_t ntn, int RC
 
 // Tuned shape: bit 0 halves the source tile, bit 1 halves the cap of the
 // target block (more source groups per target).
-static void ksum_dd(const smash_h2 *h, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
+static void ksum_dd(const smash_h2 *h, int kid, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
                     cudaStream_t s) {
-    const int kid = h->kernel_id, dim = h->dim;
+    const int dim = h->dim;
     a.nchunks = a.ldq / RC;
     int tbp = 32;
     while (tbp < max_targets && tbp * 2 * a.nchunks <= kDdThreads) tbp *= 2;
@@ -413,7 +413,7 @@ static void ksum_dd(const smash_h2 *h, bool exact, KsumDDArgs a, int64_t ntn, in
 
 // ------------------------------------------------------------------ transfers (FP64)
 // The upward and downward passes are HBM-bound and stay in FP64.
-void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof) {
+void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof, int kid) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
     int ldq, RC;
@@ -443,7 +443,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs_x3; a.ys = h->ys_x3; a.qv = qs2; a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq;
-        ksum_dd(h, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum_dd(h, kid, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
     matvec_upward(h, qs, qhat, ldq, s);
@@ -457,7 +457,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         a.xt = exact ? R.skel_x3 : R.skel_dd;
         a.ys = exact ? Cs.skel_x3 : Cs.skel_dd;
         a.qv = qhat2; a.out = zhat; a.scale = exact ? ldexp(1.0, -h->dd_e) : scale; a.ldq = ldq;
-        ksum_dd(h, exact, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum_dd(h, kid, exact, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

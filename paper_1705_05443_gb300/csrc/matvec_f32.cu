@@ -203,6 +203,8 @@ template <bool KAHAN>
 static void dispatch_f32(int kid, int dim, KsumF32Args a, int64_t ntn, int RC, cudaStream_t s) {
     switch (kid) {
     case SMASH_K_CAUCHY1D: launch_f32<SMASH_K_CAUCHY1D, 1, KAHAN>(a, ntn, RC, s); return;
+    case SMASH_K_DLP1: launch_f32<SMASH_K_DLP1, 2, KAHAN>(a, ntn, RC, s); return;  // dim == 2
+    case SMASH_K_DLP2: launch_f32<SMASH_K_DLP2, 2, KAHAN>(a, ntn, RC, s); return;
     case SMASH_K_LOG:
         if (dim == 3) launch_f32<SMASH_K_LOG, 3, KAHAN>(a, ntn, RC, s);
         else if (dim == 2) launch_f32<SMASH_K_LOG, 2, KAHAN>(a, ntn, RC, s);
@@ -221,13 +223,13 @@ static void dispatch_f32(int kid, int dim, KsumF32Args a, int64_t ntn, int RC, c
     }
 }
 
-static void ksum_f32(const smash_h2 *h, bool kahan, KsumF32Args a, int64_t ntn, int max_targets, int RC,
+static void ksum_f32(const smash_h2 *h, int kid, bool kahan, KsumF32Args a, int64_t ntn, int max_targets, int RC,
                      cudaStream_t s) {
     a.nchunks = a.ldq / RC;
     int tbp = 32;
     while (tbp < max_targets && tbp * 2 * a.nchunks <= kF32Threads) tbp *= 2;
     if (tbp * a.nchunks > kF32Threads) tbp = std::max(1, kF32Threads / a.nchunks);
-    const bool mult = h->kernel_id == SMASH_K_INVR || h->kernel_id == SMASH_K_CAUCHY1D;
+    const bool mult = kid == SMASH_K_INVR || kid == SMASH_K_CAUCHY1D || kid == SMASH_K_DLP1 || kid == SMASH_K_DLP2;
     a.scale = mult ? 1.0 / h->s : 1.0;
     a.s_f = (float)h->s;
     a.inv_s = (float)(1.0 / h->s);
@@ -240,12 +242,12 @@ static void ksum_f32(const smash_h2 *h, bool kahan, KsumF32Args a, int64_t ntn, 
         b.tile = (c & 1) ? kF32Tile / 2 : kF32Tile;
         b.tbp = (c & 2) ? tbp / 2 : tbp;
         if (kahan)
-            dispatch_f32<true>(h->kernel_id, h->dim, b, ntn, RC, s);
+            dispatch_f32<true>(kid, h->dim, b, ntn, RC, s);
         else
-            dispatch_f32<false>(h->kernel_id, h->dim, b, ntn, RC, s);
+            dispatch_f32<false>(kid, h->dim, b, ntn, RC, s);
     };
     char key[160];
-    std::snprintf(key, sizeof(key), "ksum_f32/sm%d/k%d/d%d/c%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, h->kernel_id,
+    std::snprintf(key, sizeof(key), "ksum_f32/sm%d/k%d/d%d/c%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, kid,
                   h->dim, kahan ? 1 : 0, RC, a.ldq, pow2_at_least(max_targets), pow2_at_least(ntn));
     tune_choose(key, cands, 0, s, run);
 }
@@ -262,7 +264,7 @@ static void to_f32(const double *in, int64_t n, float *out, cudaStream_t s) {
 }
 
 void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof,
-                int precision) {
+                int precision, int kid) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
     int ldq, RC;
@@ -291,20 +293,20 @@ void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs_dd; a.ys = h->ys_dd; a.qv = qs1; a.out = zs; a.ldq = ldq;
-        ksum_f32(h, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        ksum_f32(h, kid, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
     matvec_upward(h, qs, qhat, ldq, s);
     to_f32(qhat, Cs.total_skel * ldq, qhat1, s);
     tm.mark();
     if (h->nnodes > h->nroots && precision != SMASH_PREC_F32) {
-        coupling_tc(h, precision, qhat1, zhat, ldq, s);
+        coupling_tc(h, precision, qhat1, zhat, ldq, s, kid);
     } else if (h->nnodes > h->nroots) {
         KsumF32Args a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
         a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.qv = qhat1; a.out = zhat; a.ldq = ldq;
-        ksum_f32(h, false, a, h->nnodes - h->nroots, h->r, RC, s);
+        ksum_f32(h, kid, false, a, h->nnodes - h->nroots, h->r, RC, s);
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

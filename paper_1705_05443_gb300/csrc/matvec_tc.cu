@@ -360,7 +360,8 @@ void launch_tc(int mode, const TcArgs &a, int64_t ntn, cudaStream_t s) {
 
 }  // namespace
 
-void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s) {
+void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s,
+                 int kid) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
     const int64_t ntn = h->nnodes - h->nroots;
@@ -375,7 +376,7 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
     while ((1 << a.ldq_log2) < ldq) ++a.ldq_log2;
     if ((1 << a.ldq_log2) != ldq) fail(SMASH_EINVAL, "tensor-core coupling needs a power-of-two RHS stride");
     a.nt = (ldq + 7) / 8;
-    const bool mult = h->kernel_id == SMASH_K_INVR || h->kernel_id == SMASH_K_CAUCHY1D;
+    const bool mult = kid == SMASH_K_INVR || kid == SMASH_K_CAUCHY1D || kid == SMASH_K_DLP1 || kid == SMASH_K_DLP2;
     a.scale = mult ? 1.0 / h->s : 1.0;
     a.s_f = (float)h->s;
     a.inv_s = (float)(1.0 / h->s);
@@ -386,8 +387,10 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
         b.tile = tile;
         // unused axes hold 0 in every coordinate copy, so the 3D entry serves
         // 1D and 2D points as well
-        switch (h->kernel_id) {
+        switch (kid) {
         case SMASH_K_CAUCHY1D: launch_tc<SMASH_K_CAUCHY1D, 1>(mode, b, ntn, s); return;
+        case SMASH_K_DLP1: launch_tc<SMASH_K_DLP1, 3>(mode, b, ntn, s); return;
+        case SMASH_K_DLP2: launch_tc<SMASH_K_DLP2, 3>(mode, b, ntn, s); return;
         case SMASH_K_LOG: launch_tc<SMASH_K_LOG, 3>(mode, b, ntn, s); return;
         case SMASH_K_INVR: launch_tc<SMASH_K_INVR, 3>(mode, b, ntn, s); return;
         default: launch_tc<SMASH_K_YUKAWA, 3>(mode, b, ntn, s); return;
@@ -403,7 +406,7 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
         if (sm <= 100 * 1024) dflt = tile;
     }
     char key[160];
-    std::snprintf(key, sizeof(key), "ksum_tc/sm%d/k%d/d%d/m%d/nt%d/t%lld/n%lld", h->num_sms, h->kernel_id, h->dim,
+    std::snprintf(key, sizeof(key), "ksum_tc/sm%d/k%d/d%d/m%d/nt%d/t%lld/n%lld", h->num_sms, kid, h->dim,
                   mode, a.nt, pow2_at_least(h->r), pow2_at_least(ntn));
     tune_choose(key, cands, dflt, s, run);
 }

@@ -23,6 +23,7 @@ __all__ = [
     "cauchy_1d",
     "jittered_grid",
     "cauchy_like_6_3",
+    "curve_6_4",
     "rhs",
     "sample_rows",
     "batched_problems",
@@ -92,6 +93,43 @@ def cauchy_like_6_3(n: int, seed: int, offset: float = 1e-7, p: int = 2):
     w = g.random((n, p))
     v = g.random((n, p))
     return tuple(np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, w, v))
+
+
+def curve_6_4(name: str, n: int):
+    """The boundary curves of Section 6.4 sampled for the trapezoidal rule at
+    t_j = j/n: ram head (6.10) or sunflower (6.11).  Returns a dict with the
+    points r(t_j) (n x 2), the unit outer normals (n x 2; both curves run
+    counter-clockwise, so the outer normal is (r2', -r1')/|r'|), the speeds
+    |r'(t_j)|, the signed curvatures and the weights |r'(t_j)|/n."""
+    t = np.arange(n, dtype=np.float64) / n
+    tp = 2.0 * np.pi
+    if name == "ram_head":
+        c4 = np.cos(2 * tp * t)
+        r1 = 2.0 * np.cos(tp * t)
+        r2 = 1.0 + np.sin(tp * t) - 1.4 * c4 ** 4
+        d1 = -2.0 * tp * np.sin(tp * t)
+        # d/dt cos^4(4 pi t) = -16 pi cos^3 sin
+        d2 = tp * np.cos(tp * t) + 1.4 * 4 * c4 ** 3 * (2 * tp) * np.sin(2 * tp * t)
+        dd1 = -2.0 * tp ** 2 * np.cos(tp * t)
+        s4 = np.sin(2 * tp * t)
+        dd2 = (-tp ** 2 * np.sin(tp * t)
+               + 1.4 * 4 * (2 * tp) ** 2 * (c4 ** 3 * np.cos(2 * tp * t) - 3 * c4 ** 2 * s4 ** 2))
+    elif name == "sunflower":
+        rho = 1.3 + 1.25 * np.cos(20 * tp * t)
+        drho = -1.25 * 20 * tp * np.sin(20 * tp * t)
+        ddrho = -1.25 * (20 * tp) ** 2 * np.cos(20 * tp * t)
+        c, s = np.cos(tp * t), np.sin(tp * t)
+        r1, r2 = rho * c, rho * s
+        d1 = drho * c - rho * tp * s
+        d2 = drho * s + rho * tp * c
+        dd1 = ddrho * c - 2 * drho * tp * s - rho * tp ** 2 * c
+        dd2 = ddrho * s + 2 * drho * tp * c - rho * tp ** 2 * s
+    else:
+        raise ValueError(name)
+    speed = np.sqrt(d1 ** 2 + d2 ** 2)
+    return dict(x=np.ascontiguousarray(np.stack([r1, r2], axis=1)),
+                nu=np.ascontiguousarray(np.stack([d2 / speed, -d1 / speed], axis=1)),
+                speed=speed, curvature=(d1 * dd2 - d2 * dd1) / speed ** 3, w=speed / n)
 
 
 def jittered_grid(cells_per_dim: int, d: int, seed: int, per_cell: int = 1) -> np.ndarray:
@@ -166,6 +204,7 @@ def group_by_dimension(problems: list) -> dict:
 # Kernel identifiers shared by convention (the C-ABI header and the oracle
 # each define their own copy of these numbers).
 KERNEL_LOG, KERNEL_INVR, KERNEL_YUKAWA, KERNEL_CAUCHY = 0, 1, 2, 3
+KERNEL_DLP1, KERNEL_DLP2 = 4, 5
 
 # The named workloads: point-cloud recipe plus method parameters.
 WORKLOADS = {

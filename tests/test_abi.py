@@ -159,3 +159,15 @@ def test_cauchy_like_rejects_bad_arguments_without_a_device():
     lib = sm.load_library()
     assert lib.smash_matvec_cauchy_like(None, None, None, 2, None, None, 1, 0, None) == 1
     assert "NULL" in lib.smash_last_error().decode()
+
+
+def test_double_layer_kernels_need_two_dimensions():
+    import numpy as np
+    lib = sm.load_library()
+    x = np.random.default_rng(2).random((16, 3))
+    h = C.c_void_p(12345)
+    st = lib.smash_build(C.c_void_p(x.ctypes.data), 3, 16, sm.SMASH_K_DLP1, 8, 3, 1e-8, C.byref(h))
+    assert st == 1 and h.value is None
+    assert "dim == 2" in lib.smash_last_error().decode()
+    assert lib.smash_matvec_double_layer(None, None, None, None, None, None, 1, 0, None) == 1
+    assert lib.smash_matvec_kernel(None, 4, None, None, 1, 0, None) == 1

@@ -574,3 +574,45 @@ def test_h2_matvec_on_selected_leaves_equals_full_matvec():
     assert np.array_equal(zsel[rows], zall[rows])
     others = np.setdiff1d(np.arange(5000), rows)
     assert np.all(np.isnan(zsel[others]))
+
+
+# ---------------------------------------------------------------- Section 6.4 kernels
+def _double_layer_dense(c, pts, rows=None):
+    """sum_a kernel_a(x, y_j) nu_a(y_j) w_j for the oracle's gradient kernels."""
+    x, nu, w = c["x"], c["nu"], c["w"]
+    q1 = np.ascontiguousarray((nu[:, 0] * w)[:, None])
+    q2 = np.ascontiguousarray((nu[:, 1] * w)[:, None])
+    return (oracle.dense_rows(pts, 4, q1, rows=rows, y=x) + oracle.dense_rows(pts, 5, q2, rows=rows, y=x)).ravel()
+
+
+@pytest.mark.parametrize("name,inside,n", [("ram_head", (0.1, 0.1), 2000), ("sunflower", (1.5, 0.0), 40000)])
+def test_gradient_kernels_satisfy_gauss_integral(name, inside, n):
+    """Gauss's integral for the double layer of Section 6.4 with
+    Phi = -(1/2 pi) log|x - y| and outer normals: int_Gamma dPhi/dnu_y ds_y is
+    -1 inside the domain, 0 outside and -1/2 on the (smooth) boundary.  The
+    trapezoidal rule on these periodic curves converges spectrally; on the
+    curve the Nystrom diagonal is the kernel's limit -curvature/(4 pi) times
+    the weight.  A wrong sign, factor or component of the kernels fails."""
+    c = si.curve_6_4(name, n)
+    v_in = _double_layer_dense(c, np.array([inside]))
+    v_out = _double_layer_dense(c, np.array([[5.0, 5.0]]))
+    assert abs(v_in[0] + 1.0) < 1e-12
+    assert abs(v_out[0]) < 1e-12
+    rows = np.arange(0, n, n // 50)
+    on = _double_layer_dense(c, c["x"], rows=rows) - c["curvature"][rows] / (4 * np.pi) * c["w"][rows]
+    assert np.max(np.abs(on + 0.5)) < 1e-7
+
+
+def test_gradient_kernels_are_antisymmetric_and_h2_converges():
+    """kernel_a(x, y) = -kernel_a(y, x) (the gradient of a symmetric function
+    of x - y), and the oracle's H^2 matrix of a gradient kernel converges to
+    the dense product as the order rises."""
+    a, b = np.array([0.3, -0.2]), np.array([-1.1, 0.7])
+    for kid in (4, 5):
+        assert oracle.kernel(kid, a, b) == -oracle.kernel(kid, b, a)
+        assert oracle.kernel(kid, a, a) == 0.0
+    c = si.curve_6_4("ram_head", 3000)
+    q = si.rhs(3000, 2, 7000)
+    zd = oracle.dense_rows(c["x"], 4, q)
+    errs = [rel(oracle.H2(c["x"], 4, 50, p, 1e-14).matvec(q), zd) for p in (4, 6, 8)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-12, errs
