@@ -40,6 +40,10 @@ NUM_SMS = 152
 PAIR_EVAL_FLOPS = 9        # FP64: squared distance (8) + reciprocal square root (1) per kernel entry
 DD_EVAL_OPS = 54           # double-float: FP32 instructions of one 1/|x-y| entry (difference, square, rsqrt + Newton)
 DD_MAC_OPS = 12            # double-float: FP32 instructions of one error-free multiply-accumulate
+# DRAM bytes of one double-float coupling launch (3D 1/r, N = 2^18, 16 RHS,
+# 6.099e9 entries) from ncu (profiles/ksum_dd_coupling_3d_invr_262144.md);
+# scaled to other sizes by the entries of the launch
+DD_COUPLING_TRAFFIC = (53.276672e6 + 13.297408e6, 6099084090)
 F32_EVAL_OPS = 14          # FP32: two-float difference (9), squared distance (3), rsqrt + select (2)
 
 
@@ -393,7 +397,8 @@ def bench_ours(args, w):
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
 
-    prec = {"f32x2": sm.SMASH_PREC_F32X2, "f64": sm.SMASH_PREC_F64, "f32": sm.SMASH_PREC_F32}[args.precision]
+    prec = {"f32x2": sm.SMASH_PREC_F32X2, "f64": sm.SMASH_PREC_F64, "f32": sm.SMASH_PREC_F32,
+            "tf32": sm.SMASH_PREC_TF32, "bf16": sm.SMASH_PREC_BF16, "tf32x3": sm.SMASH_PREC_TF32X3}[args.precision]
 
     def step(host=False, precision=prec):
         if host:
@@ -503,6 +508,16 @@ def bench_ours(args, w):
         psrc = (f"FP64 {FP64_FLOPS_PER_CLK_SM} flop/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
                 "(nominal unit count, sampled clock; an FMA probe measured 1.19 TFLOP/s)")
         wdef = f"per kernel entry 2*nrhs + {PAIR_EVAL_FLOPS} FP64 flops"
+    elif prec in (sm.SMASH_PREC_TF32, sm.SMASH_PREC_BF16, sm.SMASH_PREC_TF32X3):
+        # the products run on the tensor pipe; the FP32 pipe evaluates the entries
+        cvt = {sm.SMASH_PREC_TF32: 1, sm.SMASH_PREC_BF16: 1, sm.SMASH_PREC_TF32X3: 3}[prec]
+        peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        cpl_work = info["coupling_pairs"] * (F32_EVAL_OPS + cvt)
+        kname = "coupling (ksum_tc_kernel over L, entries on the FP32 pipe, products on the tensor cores)"
+        psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                "(the entry evaluation bounds this kernel; ncu: tensor pipe < 10 % active)")
+        wdef = (f"per kernel entry {F32_EVAL_OPS} FP32 instructions of the entry + {cvt} rounding to the "
+                "product format; the MMA products are not counted")
     elif prec == sm.SMASH_PREC_F32:
         peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         cpl_work = info["coupling_pairs"] * (nrhs + F32_EVAL_OPS)
@@ -519,6 +534,9 @@ def bench_ours(args, w):
         wdef = (f"per kernel entry {DD_MAC_OPS}*nrhs + {DD_EVAL_OPS} FP32 instructions of the "
                 "double-float algorithm (error-free products and sums)")
     achieved = cpl_work / (cpl_ms / 1e3) / 1e12
+    traffic = None
+    if prec == sm.SMASH_PREC_F32X2 and args.workload == "3d_invr_1m":
+        traffic = DD_COUPLING_TRAFFIC[0] * info["coupling_pairs"] / DD_COUPLING_TRAFFIC[1]
     mixed = run_mixed(sm, torch, dev) if args.mixed else None
     batched = None
     if args.batched:
@@ -533,7 +551,8 @@ def bench_ours(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {sm.SMASH_PREC_F32X2: "f32x2", sm.SMASH_PREC_F64: "f64", sm.SMASH_PREC_F32: "f32"}[prec],
+        "dtype": {sm.SMASH_PREC_F32X2: "f32x2", sm.SMASH_PREC_F64: "f64", sm.SMASH_PREC_F32: "f32",
+                  sm.SMASH_PREC_TF32: "tf32", sm.SMASH_PREC_BF16: "bf16", sm.SMASH_PREC_TF32X3: "tf32x3"}[prec],
         "data": "synthetic",
         "config": {"workload": (args.workload if args.workload != "3d_invr_1m" else "3d_invr uniform cube N=2^20")
                    + ("" if n == 1 << 20 else f" at N={n}"),
@@ -542,11 +561,18 @@ def bench_ours(args, w):
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
                    "precision": "build fp64; matvec " + {sm.SMASH_PREC_F64: "fp64",
                                                           sm.SMASH_PREC_F32X2: "double-float kernel sums, fp64 transfers",
-                                                          sm.SMASH_PREC_F32: "fp32 kernel sums, fp64 transfers"}[prec],
+                                                          sm.SMASH_PREC_F32: "fp32 kernel sums, fp64 transfers",
+                                                          sm.SMASH_PREC_TF32: "tf32 coupling products, fp32 near field",
+                                                          sm.SMASH_PREC_BF16: "bf16 coupling products, fp32 near field",
+                                                          sm.SMASH_PREC_TF32X3: "split-tf32 coupling products, "
+                                                                                "fp32 near field"}[prec],
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": psrc, "work_definition": wdef,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": None if traffic is None else
+                     "ncu dram__bytes_read+write of the N=2^18 launch, scaled by kernel entries",
+                     "peak_source": psrc, "work_definition": wdef,
                      "work_per_launch": cpl_work, "ms_per_launch": cpl_ms},
         "fp64_matvec_step": None if fp64_ms is None else {"ms_per_step": fp64_ms, "value": ws * n / (fp64_ms / 1e3)},
         "rel_diff_vs_fp64_matvec": parity,
@@ -585,7 +611,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe); for profiling cases")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0 = skip)")
-    ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64", "f32"],
+    ap.add_argument("--precision", default="f32x2", choices=["f32x2", "f64", "f32", "tf32", "bf16", "tf32x3"],
                     help="matvec arithmetic: double-float kernel sums (FP64-accurate), plain FP64, or "
                          "mixed precision FP32")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
