@@ -390,7 +390,11 @@ static smash_status matvec_impl(smash_handle h, int kid, const double *X, double
         run_matvec(h, Xd, Yd, nrhs, precision, s, &h->prof_mv, kid);
         if (yhost) CK(cudaMemcpyAsync(Y, Yd, (size_t)h->nx * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         io.release();
-        if (yhost || !stream) CK(cudaStreamSynchronize(s));
+        if (yhost || !stream) {
+            CK(cudaStreamSynchronize(s));
+            if (precision == SMASH_PREC_TF32 && tc05_take_timeouts() > 0)
+                fail(SMASH_ETIMEOUT, "a tensor-core wait gave up; the result is not valid");
+        }
         return SMASH_OK;
     } catch (const Error &e) {
         return record(e);

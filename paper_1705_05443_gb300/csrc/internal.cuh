@@ -186,6 +186,10 @@ void matvec_f32(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs,
 // times q^ (FP32, ldq per slot) in TF32/BF16/split TF32, written to zhat (FP64) x scale
 void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zhat, int ldq, cudaStream_t s,
                  int kid);
+// the TF32 coupling on tcgen05 (tensor-memory accumulator); tc05_take_timeouts
+// returns and clears the count of CTAs whose bounded mbarrier waits gave up
+void coupling_tc05(const smash_h2 *h, const float *qhat, double *zhat, int ldq, cudaStream_t s, int kid);
+int tc05_take_timeouts();
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);

@@ -32,6 +32,7 @@ constexpr int kTcThreads = 256;  // 8 warps
 constexpr int kTcMaxTile = 256;  // sources staged per round: 64, 128 or 256 (a multiple of 16)
 constexpr int kTcRows = 128;     // targets per pass: 8 warps x 16
 constexpr int kTcMaxNt = 8;      // up to 64 right-hand sides (8 n-tiles of 8)
+constexpr int kTcUseTcgen05 = 1; // tuning choice: the tcgen05 kernel instead of a warp-MMA tile
 
 struct TcArgs {
     const int32_t *tnodes;
@@ -383,6 +384,10 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
     a.log_s = (float)log(h->s);
     const int mode = precision == SMASH_PREC_BF16 ? TC_BF16 : (precision == SMASH_PREC_TF32X3 ? TC_TF32X3 : TC_TF32);
     auto run = [&](int tile) {
+        if (tile == kTcUseTcgen05) {
+            coupling_tc05(h, qhat, zhat, ldq, s, kid);
+            return;
+        }
         TcArgs b = a;
         b.tile = tile;
         // unused axes hold 0 in every coordinate copy, so the 3D entry serves
@@ -405,6 +410,8 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
         if (sm <= 200 * 1024) cands.push_back(tile);
         if (sm <= 100 * 1024) dflt = tile;
     }
+    // TF32 products also have the tcgen05 kernel (tensor-memory accumulator)
+    if (mode == TC_TF32) cands.push_back(kTcUseTcgen05);
     char key[160];
     std::snprintf(key, sizeof(key), "ksum_tc/sm%d/k%d/d%d/m%d/nt%d/t%lld/n%lld", h->num_sms, kid, h->dim,
                   mode, a.nt, pow2_at_least(h->r), pow2_at_least(ntn));

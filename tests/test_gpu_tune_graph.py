@@ -147,3 +147,32 @@ def test_graph_matvec_rejects_host_buffers(clean_table):
     with pytest.raises(sm.SmashError, match="device buffers"):
         h.matvec_graph(X, np.empty_like(X))
     h.close()
+
+
+def test_tcgen05_coupling_candidate_keeps_the_tf32_bar(clean_table, tmp_path):
+    """The TF32 coupling has two kernels: warp MMAs over staged tiles and the
+    tcgen05 kernel with its accumulator in tensor memory.  Forcing the tcgen05
+    candidate through the tuning table gives the same bar against the oracle
+    (1e-3) as the default."""
+    x = si.sphere_with_caps(10000, 4500)
+    q = si.rhs(10000, 32, 4501)
+    ho = oracle.H2(x, 2, 128, 5, 1e-8)
+    zo = ho.matvec(q)
+    sm.smash_set_autotune(True)
+    h = sm.H2Matrix(_dev(x), 2, 128, 5, 1e-8)
+    h.matvec(_dev(q), precision=sm.SMASH_PREC_TF32)
+    sm.smash_set_autotune(False)
+    path = tmp_path / "t.json"
+    sm.smash_autotune_save(str(path))
+    table = json.loads(path.read_text())["entries"]
+    keys = [k for k in table if k.startswith("ksum_tc/") and "/m0/" in k]
+    assert keys
+    for choice in (1, 64):  # 1 = the tcgen05 kernel, 64 = a warp-MMA tile
+        forced = dict(table)
+        forced.update({k: choice for k in keys})
+        path.write_text(json.dumps({"smash_autotune": 1, "entries": forced}))
+        sm.smash_autotune_clear()
+        sm.smash_autotune_load(str(path))
+        z = h.matvec(_dev(q), precision=sm.SMASH_PREC_TF32).cpu().numpy()
+        assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-3, choice
+    h.close()
