@@ -53,6 +53,20 @@ def _dist():
     return ws, rank
 
 
+def replica_value(local_total_ms: float, n_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas (one per rank): all ranks'
+    points over the slowest rank's time.  Returns (value, max total ms)."""
+    import torch
+    tot = float(local_total_ms)
+    ws = 1
+    if dist is not None:
+        ws = dist.get_world_size()
+        t = torch.tensor([tot], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    return ws * n_per_rank * steps / (tot / 1e3), tot
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -462,12 +476,7 @@ def bench_ours(args, w):
     launches = sm.smash_launch_count() - launches0
     if dist:
         dist.barrier()
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * n * args.steps / (tot_ms / 1e3)
+    value, tot_ms = replica_value(sum(step_ms), n, args.steps, dist, dev)
 
     # end to end through the same C ABI with pinned host buffers
     xh = torch.from_numpy(x_np).pin_memory()
