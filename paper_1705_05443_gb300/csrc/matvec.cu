@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(kKsThreads) ksum_f64_kernel(KsumArgs a) {
     const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
     const int ldq = a.ldq;
     const int tid = threadIdx.x;
-    // targets per thread block row: the smallest power of two >= T (at least
-    // 32, at most a.tbp), the remaining threads split the sources into groups
-    int tbp = 32;
-    while (tbp < T && tbp < a.tbp) tbp *= 2;
+    // targets per thread block row: T itself (at most a.tbp), so that no lane
+    // of a group idles, but at least 16 lanes per group (at most 16 groups to
+    // reduce); the remaining threads split the sources into groups
+    const int tbp = min(max(T, (16 + a.nchunks - 1) / a.nchunks), a.tbp);
     const int groups = kKsThreads / (tbp * a.nchunks);
     const int per_group = tbp * a.nchunks;
     const int grp = tid / per_group;

@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
     const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
     const int ldq = a.ldq;
     const int tid = threadIdx.x;
-    int tbp = 32;  // thread rows; each covers TA targets
-    while (tbp * TA < T && tbp < a.tbp) tbp *= 2;
+    // thread rows, each covering TA targets: as many as T needs (at most a.tbp,
+    // at least 16 lanes per group)
+    const int tbp = min(max((T + TA - 1) / TA, (16 + a.nchunks - 1) / a.nchunks), a.tbp);
     const int groups = kF32Threads / (tbp * a.nchunks);
     const int per_group = tbp * a.nchunks;
     const int grp = tid / per_group;
