@@ -220,8 +220,11 @@ constexpr int kDdThreads = 256;
 constexpr int kDdTile = 128;
 constexpr int kDdTileMax = 256;
 
+// Up to 16 RHS per chunk the kernel fits 80 registers, so three CTAs share an
+// SM and hide the latencies of the dependent double-float chains; 32 RHS
+// need about twice the accumulators and run at one CTA per SM.
 template <int KID, int D, int RC, bool EXACT>
-__global__ void __launch_bounds__(kDdThreads) ksum_dd_kernel(KsumDDArgs a) {
+__global__ void __launch_bounds__(kDdThreads, RC <= 16 ? 3 : 1) ksum_dd_kernel(KsumDDArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
     constexpr int NC = EXACT ? 3 : 2;                                 // float4 per point

@@ -49,7 +49,7 @@ constexpr int kF32Tile = 256;
 // source are read from shared memory as float4 (RC >= 4) and reused by the
 // TA targets.
 template <int KID, int D, int RC, bool KAHAN, int TA>
-__global__ void __launch_bounds__(kF32Threads) ksum_f32_kernel(KsumF32Args a) {
+__global__ void __launch_bounds__(kF32Threads, (KAHAN && RC >= 32) || (!KAHAN && RC == 16) ? 2 : 3) ksum_f32_kernel(KsumF32Args a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
     const int tile = a.tile;                                      // <= kF32Tile
