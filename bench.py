@@ -43,7 +43,7 @@ DD_MAC_OPS = 12            # double-float: FP32 instructions of one error-free m
 # DRAM bytes of one double-float coupling launch (3D 1/r, N = 2^18, 16 RHS,
 # 6.099e9 entries) from ncu (profiles/ksum_dd_coupling_3d_invr_262144.md);
 # scaled to other sizes by the entries of the launch
-DD_COUPLING_TRAFFIC = (53.540608e6 + 13.356288e6, 6099084090)
+DD_COUPLING_TRAFFIC = (53.189376e6 + 13.053952e6, 6099084090)
 F32_EVAL_OPS = 14          # FP32: two-float difference (9), squared distance (3), rsqrt + select (2)
 
 
