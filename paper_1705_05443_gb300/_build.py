@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
           "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", SRC]
-NO_FMA = {"tree.cu", "compress.cu", "matvec_dd.cu"}
+NO_FMA = {"tree.cu", "compress.cu", "matvec_dd.cu", "matvec_oz.cu"}
 
 
 def _nvcc() -> str:

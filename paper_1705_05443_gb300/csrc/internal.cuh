@@ -190,6 +190,11 @@ void coupling_tc(const smash_h2 *h, int precision, const float *qhat, double *zh
 // returns and clears the count of CTAs whose bounded mbarrier waits gave up
 void coupling_tc05(const smash_h2 *h, const float *qhat, double *zhat, int ldq, cudaStream_t s, int kid);
 int tc05_take_timeouts();
+// the double-float coupling with its products on the tensor cores (exact
+// 8-bit digit splits of the entries and of q^, FP64 q^ in, FP64 zhat out);
+// supported for one problem of at most 10 levels, tau < 1, ldq <= 16
+bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq);
+void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s);
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);

@@ -32,38 +32,14 @@
 //    tile, and written out in FP64.
 // Compiled with --fmad=false: every fused operation below is an explicit fmaf.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
+#include "dd_arith.cuh"
 #include "internal.cuh"
 #include "ksum_tiles.cuh"
 
 namespace smash {
-
-// ------------------------------------------------------------------ error-free transforms
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// requires |a| >= |b| (or a == 0)
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    e = b - (s - a);
-}
-
-// The same s and e as two_sum: with the operands ordered by magnitude the
-// three-operation form above is exact (Dekker), so the error term -- which
-// is unique -- comes out bit for bit equal.  The compare and the two selects
-// issue on the ALU pipe, leaving three operations on the FP32 pipe instead
-// of six.
-__device__ __forceinline__ void two_sum_ordered(float a, float b, float &s, float &e) {
-    const bool a_big = fabsf(a) >= fabsf(b);
-    const float big = a_big ? a : b;
-    const float small = a_big ? b : a;
-    s = a + b;
-    e = small - (s - big);
-}
 
 // ------------------------------------------------------------------ conversions
 // per point: (hi x, hi y, hi z, 0, lo x, lo y, lo z, 0) of x'' = 1 + (x - lo)/s
@@ -145,56 +121,6 @@ __device__ __forceinline__ void diff3(float xh, float xm, float xl, float yh, fl
     two_sum_ordered(a, b, s, t);
     t = t + ((ea + eb) + c);
     fast_two_sum(s, t, dh, dl);
-}
-
-// ------------------------------------------------------------------ kernel entries
-// kappa'' = 1/|d| (3D/2D/1D) or 1/d (Cauchy, 1D) in double-float; d = (dh + dl) per axis.
-template <int KID, int D>
-__device__ __forceinline__ void kappa_dd(const float *dh, const float *dl, float &kh, float &kl) {
-    if (KID == SMASH_K_CAUCHY1D) {
-        float h = dh[0], l = dl[0];
-        float dsum, derr;
-        fast_two_sum(h, l, dsum, derr);  // |h| >= |l| unless h == 0
-        if (dsum == 0.f && derr == 0.f) { kh = 0.f; kl = 0.f; return; }
-        float y0 = __frcp_rn(dsum);
-        float uh = dsum * y0;
-        float ul = fmaf(dsum, y0, -uh);
-        ul = fmaf(derr, y0, ul);
-        float ee = (1.0f - uh) - ul;
-        float c = y0 * ee;
-        fast_two_sum(y0, c, kh, kl);
-        return;
-    }
-    // r2 = sum_a (dh + dl)^2 as a double-float
-    float p[3], e[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a < D) {
-            p[a] = dh[a] * dh[a];
-            float t = fmaf(dh[a], dh[a], -p[a]);
-            t = fmaf(2.0f * dh[a], dl[a], t);
-            e[a] = fmaf(dl[a], dl[a], t);
-        } else {
-            p[a] = 0.f;
-            e[a] = 0.f;
-        }
-    }
-    float s1, t1, rh, t2;
-    two_sum_ordered(p[0], p[1], s1, t1);
-    two_sum_ordered(s1, p[2], rh, t2);
-    float rl = ((e[0] + e[1]) + (e[2] + t1)) + t2;
-    fast_two_sum(rh, rl, rh, rl);
-    if (rh == 0.f) { kh = 0.f; kl = 0.f; return; }
-    float y0 = rsqrtf(rh);
-    float th = y0 * y0;
-    float tl = fmaf(y0, y0, -th);
-    float uh = rh * th;
-    float ul = fmaf(rh, th, -uh);
-    ul = fmaf(rh, tl, ul);
-    ul = fmaf(rl, th, ul);
-    float ee = (1.0f - uh) - ul;
-    float c = y0 * (0.5f * ee);
-    fast_two_sum(y0, c, kh, kl);
 }
 
 // ------------------------------------------------------------------ kernel sums
@@ -450,9 +376,12 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
     }
     tm.mark();
     matvec_upward(h, qs, qhat, ldq, s);
-    dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
     tm.mark();
-    if (h->nnodes > h->nroots) {
+    // the coupling: products on the tensor cores (exact digit splits) where
+    // the tree allows it, else every operation in double-float on the FP32
+    // pipe; the tuner may take either
+    auto dd_coupling = [&] {
+        dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
         KsumDDArgs a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
@@ -461,6 +390,19 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         a.ys = exact ? Cs.skel_x3 : Cs.skel_dd;
         a.qv = qhat2; a.out = zhat; a.scale = exact ? ldexp(1.0, -h->dd_e) : scale; a.ldq = ldq;
         ksum_dd(h, kid, exact, a, h->nnodes - h->nroots, h->r, RC, s);
+    };
+    if (h->nnodes > h->nroots) {
+        if (coupling_oz_supported(h, kid, ldq)) {
+            char key[128];
+            std::snprintf(key, sizeof(key), "coupling_dd/sm%d/k%d/d%d/ld%d/n%lld", h->num_sms, kid, h->dim, ldq,
+                          pow2_at_least(h->nnodes));
+            tune_choose(key, {0, 1}, 0, s, [&](int c) {
+                if (c == 0) coupling_oz(h, kid, qhat, zhat, ldq, s);
+                else dd_coupling();
+            });
+        } else {
+            dd_coupling();
+        }
     }
     tm.mark();
     matvec_downward(h, zhat, zs, ldq, s);

@@ -1,0 +1,609 @@
+// matvec_oz.cu -- the coupling (3.19) of the double-float matvec with its
+// multiply-accumulate on the tensor cores, split exactly into 8-bit digits.
+//
+// The coupling z^_i += sum_{j in L(i)} K(X^_i, Y^_j) q^_j is a dense
+// contraction per target node: kernel entries (generated, ~2^-46 relative
+// precision, double-float) times the skeleton vectors q^ (FP64).  Here both
+// operands are written as short sums of 8-bit integer digits, every product
+// of two digits is formed and summed on the tensor cores without rounding,
+// and only the combination of the digit levels is done in double-float:
+//
+//  * Entries.  For a target node i, every entry of its row block is bounded by
+//    the admissibility geometry (Def. 2.1, (2.3)): points lie in their cells,
+//    so |x - y| >= |c_i - c_j| - r_i - r_j >= (1 - tau) |c_i - c_j| > 0 for the
+//    cell centres c and half-diagonals r (tau < 1), and |x - y| is at least the
+//    distance from the target point x to the partner's cell.  With 2^E_x above
+//    twice the smaller of the two bounds over the row of x, K' = K 2^-E_x lies
+//    in (-1/2, 1/2) and is split as K' = sum_{s<6} a_s 2^{-8(s+1)} with integers
+//    |a_s| <= 128 (round-to-nearest digits; the first three from hi(K), the
+//    last three from the rest).
+//  * Vectors.  Per tree level l and column c, 2^F_lc above twice the largest
+//    |q^_jc| of the level's skeletons scales q^ into (-1/2, 1/2);
+//    q' = sum_{t<6} b_t 2^{-8(t+1)}, |b_t| <= 128, in FP64 once.  A row of L
+//    lists its partners by level, so a tile never mixes two levels.
+//  * Products.  K' q' = sum_L 2^{-8L-16} sum_{s+t=L} a_s b_t, truncated at
+//    L <= 5 (dropped terms below 2^-47 relative).  A digit product is at most
+//    2^14 and a level holds at most 6 of them, so 128 sources sum to less
+//    than 2^24: the FP32 accumulation of bf16 x bf16 products
+//    (mma.sync m16n8k16) is exact for every level.  After each tile (at most
+//    128 sources per warp) the six level sums are combined by error-free
+//    transformations, scaled by 2^(F_lc - max_l F_lc) (exact), into a
+//    double-float accumulator per output.
+//
+// The result keeps the double-float coupling's precision (~2^-46 per entry)
+// while the FP32 pipe evaluates only the entries and their digits; the
+// products move to the tensor cores.  Used for the normalised two-float
+// coordinates (trees of at most 10 levels, one problem) with at most 16
+// right-hand sides per pass.
+// Compiled with --fmad=false: every fused operation below is an explicit fmaf.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include <cuda_bf16.h>
+
+#include "dd_arith.cuh"
+#include "internal.cuh"
+#include "ksum_tiles.cuh"
+
+namespace smash {
+
+constexpr int kOzDigits = 6;
+constexpr int kOzThreads = 256;
+constexpr int kOzTileCap = 256;  // sources per tile (two or more warps per row tile)
+constexpr int kOzRows = 128;     // targets per pass (8 row tiles of 16)
+
+// ------------------------------------------------------------------ q^ digits
+constexpr int kOzLevels = 16;  // rows of the per-level tables (levels 0..10 on this path)
+
+// max |q^_jc| per (level, column), one warp per node; non-negative doubles
+// order as their bit patterns
+__global__ void oz_colmax_kernel(const double *__restrict__ q, int ldq, int64_t nnodes,
+                                 const int32_t *__restrict__ level, const int32_t *__restrict__ k,
+                                 const int64_t *__restrict__ sk_off, unsigned long long *__restrict__ cmax) {
+    __shared__ unsigned long long sm[kOzLevels * 16];
+    for (int i = threadIdx.x; i < kOzLevels * 16; i += blockDim.x) sm[i] = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t g = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); g < nnodes; g += (int64_t)gridDim.x * wpb) {
+        const int kk = k[g];
+        const double *qg = q + sk_off[g] * ldq;
+        unsigned long long m = 0ull;
+        for (int e = lane; e < kk * ldq; e += 32) {  // lane keeps column lane % ldq
+            const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(qg[e]));
+            m = b > m ? b : m;
+        }
+        for (int o = 16; o >= ldq; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y > m ? y : m;
+        }
+        if (lane < ldq && m) atomicMax(&sm[level[g] * 16 + lane], m);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOzLevels * 16; i += blockDim.x)
+        if (sm[i]) atomicMax(&cmax[i], sm[i]);
+}
+
+// F_lc = ilogb(max) + 2 puts the level's values in (-1/2, 1/2); fref_c is the
+// largest over the levels, fd[l][c] = F_lc - fref_c (levels without values:
+// 0; at most 60 below fref_c, which only loses digits of values that small)
+__global__ void oz_scales_kernel(const unsigned long long *__restrict__ cmax, int *__restrict__ fd,
+                                 int *__restrict__ fref, double *__restrict__ colscale) {
+    const int c = threadIdx.x;
+    if (c >= 16) return;
+    int fr = 0;
+    bool any = false;
+    for (int l = 0; l < kOzLevels; ++l) {
+        const unsigned long long m = cmax[l * 16 + c];
+        if (!m) continue;
+        const int f = ilogb(__longlong_as_double((long long)m)) + 2;
+        fr = any ? max(fr, f) : f;
+        any = true;
+    }
+    for (int l = 0; l < kOzLevels; ++l) {
+        const unsigned long long m = cmax[l * 16 + c];
+        const int f = m ? max(ilogb(__longlong_as_double((long long)m)) + 2, fr - 60) : fr;
+        fd[l * 16 + c] = f - fr;
+    }
+    fref[c] = fr;
+    colscale[c] = ldexp(1.0, fr);
+}
+
+// dig[(slot * 6 + t) * NC + c] = b_t of q^_slot,c 2^-F_lc (zero for c >= ldq),
+// one warp per node
+__global__ void oz_digits_kernel(const double *__restrict__ q, int ldq, int NC, int64_t nnodes,
+                                 const int32_t *__restrict__ level, const int32_t *__restrict__ k,
+                                 const int64_t *__restrict__ sk_off, const int *__restrict__ fd,
+                                 const int *__restrict__ fref, __nv_bfloat16 *__restrict__ dig) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t g = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); g < nnodes; g += (int64_t)gridDim.x * wpb) {
+        const int kk = k[g], lv = level[g];
+        const int64_t base = sk_off[g];
+        for (int e = lane; e < kk * NC; e += 32) {
+            const int t = e / NC, c = e - t * NC;
+            const int64_t slot = base + t;
+            double x = 0.0;
+            if (c < ldq) x = ldexp(q[slot * ldq + c], -(fref[c] + fd[lv * 16 + c]));
+#pragma unroll
+            for (int u = 0; u < kOzDigits; ++u) {
+                x *= 256.0;
+                const double d = rint(x);
+                x -= d;  // exact: |x - d| <= 1/2 carries the low bits of x
+                dig[(slot * kOzDigits + u) * NC + c] = __float2bfloat16_rn((float)d);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core helpers
+__device__ __forceinline__ uint32_t oz_pack(float first, float second) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+    return r;
+}
+
+__device__ __forceinline__ void oz_mma(float *c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                       uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void oz_ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                                 uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void oz_ldsm_x2_trans(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+__device__ __forceinline__ void oz_cp16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+
+__device__ __forceinline__ void oz_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// round to the nearest integer (|x| < 2^22) by the 1.5 * 2^23 shift
+constexpr float kOzShift = 12582912.0f;
+
+// ------------------------------------------------------------------ coupling kernel
+struct KsumOzArgs {
+    const int32_t *tnodes;
+    const int64_t *t_off;
+    const int32_t *t_cnt;
+    const int64_t *ptr;
+    const int32_t *col;
+    const int64_t *s_off;
+    const int32_t *s_cnt;
+    const float *xt;           // target normalised coordinates, 8 floats per slot
+    const float *ys;           // source normalised coordinates, 8 floats per slot
+    const __nv_bfloat16 *dig;  // source digits, 6 * NC per slot
+    const int *fd;             // F_lc - fref_c, kOzLevels x 16
+    const double *colscale;    // 2^fref_c
+    const int32_t *level;
+    const uint64_t *cell;
+    double *out;               // target vectors (FP64), ldq
+    double scale;              // 1/s
+    int ldq, dim;
+};
+
+// digit bytes per source in shared memory: 6 * NC bf16 plus 16 bytes of pad,
+// which puts the 8 rows of an ldmatrix on distinct banks
+template <int NC>
+struct OzLayout {
+    static constexpr int kDigitBytes = kOzDigits * NC * 2;
+    static constexpr int kStride = kDigitBytes + 16;
+    static constexpr size_t kCoords = sizeof(float4) * 2 * kOzTileCap;
+    static constexpr size_t kDigits = (size_t)kStride * kOzTileCap;
+    static constexpr size_t kIdx = sizeof(int64_t) * kOzTileCap;
+    static constexpr size_t kRed = sizeof(double) * kOzRows * NC;
+    static constexpr size_t kAcc = sizeof(float) * 2 * (NC / 2) * kOzThreads;  // (hi, lo) per output per thread
+    static constexpr size_t kBytes = kCoords + kDigits + kIdx + kRed + kAcc;
+};
+
+// bound of target node g's row from the cells alone: max over partners j of
+// 1 / (|c_g - c_j| - r_g - r_j) in the unit frame of the normalised coordinates
+// (the root, level 1, is the unit cube; a level-l cell has width 2^(1-l))
+__device__ double oz_node_bound(const KsumOzArgs &a, int64_t g, int64_t e0, int64_t e1, unsigned long long *slot) {
+    const int d = a.dim;
+    const int li = a.level[g];
+    const uint64_t *ci = a.cell + g * 3;
+    unsigned long long best = 0ull;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kOzThreads) {
+        const int64_t j = a.col[e];
+        const int lj = a.level[j];
+        const uint64_t *cj = a.cell + j * 3;
+        const int m = li > lj ? li : lj;
+        // centres (2c + 1) 2^(m - l) and radii sqrt(d) 2^(m - l) in units of 2^-m,
+        // half the width of a level-m cell
+        double sum = 0.0;
+        for (int ax = 0; ax < d; ++ax) {
+            const uint64_t Ci = (2 * ci[ax] + 1) << (m - li);
+            const uint64_t Cj = (2 * cj[ax] + 1) << (m - lj);
+            const double D = (double)(Ci >= Cj ? Ci - Cj : Cj - Ci);
+            sum += D * D;
+        }
+        const double rad = sqrt((double)d) * (ldexp(1.0, m - li) + ldexp(1.0, m - lj));
+        const double gap = sqrt(sum) - rad;
+        const double kb = gap > 0.0 ? ldexp(1.0, m) / gap : INFINITY;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(kb);
+        best = b > best ? b : best;
+    }
+    if (threadIdx.x == 0) *slot = 0ull;
+    __syncthreads();
+    atomicMax(slot, best);
+    __syncthreads();
+    return __longlong_as_double((long long)*slot);
+}
+
+// smallest squared distance from the point x (hi parts) to the cells of the
+// row's partners; each gap is reduced by 2^-22 to cover the lo part (< 2^-23)
+// and the roundings, so the result is a lower bound.  The four lanes of a
+// quad split the partners.
+template <int D>
+__device__ __forceinline__ float oz_point_gap2(const float4 &x, const KsumOzArgs &a, int64_t e0, int64_t e1, int t4) {
+    float best = INFINITY;
+    for (int64_t e = e0 + t4; e < e1; e += 4) {
+        const int64_t j = a.col[e];
+        const float w = ldexpf(1.0f, 1 - a.level[j]);  // cell width (the root is level 1)
+        const uint64_t *cj = a.cell + j * 3;
+        const float xv[3] = {x.x, x.y, x.z};
+        float s2 = 0.f;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const float lo = fmaf((float)cj[ax], w, 1.0f);  // exact: c < 2^9, w a power of two
+            const float gap = fmaxf(fmaxf(lo - xv[ax], xv[ax] - (lo + w)) - 0x1p-22f, 0.f);
+            s2 = fmaf(gap, gap, s2);
+        }
+        best = fminf(best, s2);
+    }
+    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 1));
+    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 2));
+    return best;
+}
+
+// exponent E with K' = K 2^-E in (-1/2, 1/2) for every entry of the row of x
+__device__ __forceinline__ int oz_row_exponent(float gap2, double node_kb) {
+    float kb = (float)(node_kb * (1.0 + 1e-6));
+    if (gap2 > 0.f) kb = fminf(kb, rsqrtf(gap2) * (1.0f + 0x1p-18f));
+    return ilogbf(kb) + 2;
+}
+
+// 1/|d| in double-float for d = dh + dl, d != 0 (admissible pairs): the
+// squares exactly by FMA, their sum by magnitude-ordered Fast2Sum (the squares
+// are non-negative, so max/min order them), then one Newton step on the
+// hardware reciprocal square root with the residual 1 - r y0^2 formed by FMA
+// and the result renormalised.
+template <int D>
+__device__ __forceinline__ void oz_invr(const float *dh, const float *dl, float &kh, float &kl) {
+    float p[3], e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            p[a] = dh[a] * dh[a];
+            const float t = fmaf(dh[a], dh[a], -p[a]);
+            e[a] = fmaf(dl[a], fmaf(2.0f, dh[a], dl[a]), t);  // 2 dh dl + dl^2
+        } else {
+            p[a] = 0.f;
+            e[a] = 0.f;
+        }
+    }
+    const float s1 = p[0] + p[1];
+    const float t1 = fminf(p[0], p[1]) - (s1 - fmaxf(p[0], p[1]));
+    const float rh = s1 + p[2];
+    const float t2 = fminf(s1, p[2]) - (rh - fmaxf(s1, p[2]));
+    const float rl = ((e[0] + e[1]) + (e[2] + t1)) + t2;
+    const float y0 = rsqrtf(rh);
+    const float th = y0 * y0;
+    const float tl = fmaf(y0, y0, -th);
+    float ee = fmaf(-rh, th, 1.0f);
+    ee = fmaf(-rh, tl, ee);
+    ee = fmaf(-rl, th, ee);
+    // renormalised, |kl| <= ulp(kh) / 2: the digit split takes kh whole into
+    // the first three digits and kl, scaled by 2^24, into the fourth
+    fast_two_sum(y0, (0.5f * y0) * ee, kh, kl);
+}
+
+template <int KID, int D>
+__device__ __forceinline__ void oz_entry(const float4 &xh, const float4 &xl, const float4 &yh, const float4 &yl,
+                                         float &kh, float &kl) {
+    float dh[3], dl[3];
+    dh[0] = xh.x - yh.x; dh[1] = xh.y - yh.y; dh[2] = xh.z - yh.z;
+    dl[0] = xl.x - yl.x; dl[1] = xl.y - yl.y; dl[2] = xl.z - yl.z;
+    if (KID == SMASH_K_CAUCHY1D)
+        kappa_dd<KID, D>(dh, dl, kh, kl);
+    else
+        oz_invr<D>(dh, dl, kh, kl);
+}
+
+template <int KID, int D, int NT>
+__global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
+    constexpr int NC = 8 * NT;
+    using Lay = OzLayout<NC>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ PartnerChunk pc;
+    __shared__ unsigned long long bound_slot;
+    __shared__ int runend[kPartnerChunk];  // per partner: one past the last partner of its level run
+    __shared__ int plev[kPartnerChunk];
+    __shared__ int sfd[kOzLevels * 16];
+    __shared__ int rowE[kOzRows];
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                           // [2][cap]: hi, lo
+    unsigned char *sd = smraw + Lay::kCoords;                                 // [cap][stride]
+    int64_t *sidx = reinterpret_cast<int64_t *>(sd + Lay::kDigits);           // [cap]
+    double *red = reinterpret_cast<double *>(smraw + Lay::kCoords + Lay::kDigits + Lay::kIdx);  // [rows][NC]
+    // running double-float sums, touched once per tile: [2 * output + (0 hi, 1 lo)][thread]
+    float *acc = reinterpret_cast<float *>(smraw + Lay::kCoords + Lay::kDigits + Lay::kIdx + Lay::kRed);
+
+    const int64_t g = a.tnodes[blockIdx.x];
+    const int T = a.t_cnt[g];
+    if (T == 0) return;
+    const int64_t toff = a.t_off[g];
+    const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
+    const int ldq = a.ldq;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, t4 = lane & 3;
+    for (int i = tid; i < kOzLevels * 16; i += kOzThreads) sfd[i] = a.fd[i];
+
+    const double kb_node = oz_node_bound(a, g, e0, e1, &bound_slot);
+    if (!(kb_node < INFINITY)) {
+        // no finite bound: cannot happen for tau < 1 (the build rejects
+        // others); write NaN rather than a wrong sum
+        for (int q = tid; q < T * ldq; q += kOzThreads) a.out[toff * ldq + q] = NAN;
+        return;
+    }
+
+    for (int tb = 0; tb < T; tb += kOzRows) {
+        const int tcount = min(kOzRows, T - tb);
+        const int wr = (tcount + 15) / 16;  // row tiles
+        const int groups = 8 / wr;          // warps along the sources per row tile
+        const int grp = warp / wr, rt = warp % wr;
+        const bool active = grp < groups;
+        const int tile = groups == 1 ? kOzTileCap / 2 : kOzTileCap;  // <= 128 sources per warp per flush
+        const int r0 = rt * 16 + gq, r1 = r0 + 8;
+        // rows past the block take row 0's point (finite entries, discarded)
+        const int rr0 = r0 < tcount ? r0 : 0, rr1 = r1 < tcount ? r1 : 0;
+        const float4 *p0 = reinterpret_cast<const float4 *>(a.xt + (toff + tb + rr0) * 8);
+        const float4 *p1 = reinterpret_cast<const float4 *>(a.xt + (toff + tb + rr1) * 8);
+        const float4 x0h = p0[0], x0l = p0[1], x1h = p1[0], x1l = p1[1];
+        // row exponents of the thread's two targets
+        float sc0[2];  // first digit: K 2^(8-E); lo(K) enters the fourth digit at 2^24 times that
+        {
+            const int E0 = oz_row_exponent(oz_point_gap2<D>(x0h, a, e0, e1, t4), kb_node);
+            const int E1 = oz_row_exponent(oz_point_gap2<D>(x1h, a, e0, e1, t4), kb_node);
+            sc0[0] = ldexpf(1.0f, 8 - E0);
+            sc0[1] = ldexpf(1.0f, 8 - E1);
+            if (active && grp == 0 && t4 == 0) {
+                rowE[r0] = E0;
+                rowE[r1] = E1;
+            }
+        }
+        // output o = 4 n + c of the thread: row r0 (c < 2) or r1, column oz_col(o)
+        auto oz_col = [t4](int o) { return (o >> 2) * 8 + 2 * t4 + (o & 1); };
+
+#pragma unroll
+        for (int o = 0; o < NT * 4; ++o) {
+            acc[(2 * o) * kOzThreads + tid] = 0.f;
+            acc[(2 * o + 1) * kOzThreads + tid] = 0.f;
+        }
+        float C[kOzDigits][NT][4];
+#pragma unroll
+        for (int L = 0; L < kOzDigits; ++L)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) C[L][n][c] = 0.f;
+
+        for (int64_t e = e0; e < e1;) {
+            load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+            const int nchunk = pc.n, total = pc.pre[pc.n];
+            for (int q = tid; q < nchunk; q += kOzThreads) plev[q] = a.level[a.col[e + q]];
+            __syncthreads();
+            if (tid == 0) {
+                int end = nchunk;
+                for (int p = nchunk - 1; p >= 0; --p) {
+                    if (p + 1 < nchunk && plev[p + 1] != plev[p]) end = p + 1;
+                    runend[p] = end;
+                }
+            }
+            __syncthreads();
+            e += nchunk;
+            for (int pos = 0; pos < total;) {
+                // the partner holding pos; the tile ends with its level run
+                int plo = 0, phi = nchunk - 1;
+                while (plo < phi) {
+                    const int mid = (plo + phi + 1) >> 1;
+                    if (pc.pre[mid] <= pos) plo = mid;
+                    else phi = mid - 1;
+                }
+                const int lv = plev[plo];
+                const int fill = min(tile, pc.pre[runend[plo]] - pos);
+                const int nkb = (fill + 15) >> 4;
+                const int fill16 = nkb << 4;
+                for (int q = tid; q < fill; q += kOzThreads) sidx[q] = chunk_source(pc, pos + q);
+                __syncthreads();
+                // coordinates (the pad up to 16 repeats source 0) and digits (zero pad)
+                for (int q = tid; q < 2 * fill16; q += kOzThreads) {
+                    const int b = q >> 1, hl = q & 1;
+                    const int64_t src = sidx[b < fill ? b : 0];
+                    oz_cp16(sy + hl * kOzTileCap + b, a.ys + src * 8 + 4 * hl);
+                }
+                constexpr int kPieces = Lay::kDigitBytes / 16;
+                for (int q = tid; q < fill * kPieces; q += kOzThreads) {
+                    const int b = q / kPieces, p = q - b * kPieces;
+                    oz_cp16(sd + (size_t)b * Lay::kStride + 16 * p,
+                            reinterpret_cast<const unsigned char *>(a.dig) + sidx[b] * Lay::kDigitBytes + 16 * p);
+                }
+                for (int q = fill * kPieces + tid; q < fill16 * kPieces; q += kOzThreads) {
+                    const int b = q / kPieces, p = q - b * kPieces;
+                    *reinterpret_cast<uint4 *>(sd + (size_t)b * Lay::kStride + 16 * p) = make_uint4(0u, 0u, 0u, 0u);
+                }
+                oz_cp_wait_all();
+                __syncthreads();
+                if (active) {
+                    const uint32_t sd_base = (uint32_t)__cvta_generic_to_shared(sd);
+                    // ldmatrix rows: lane l addresses source kb*16 + (l & 7) + 8 ((l >> 3) & 1),
+                    // columns 8 (l >> 4) of each digit plane
+                    const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1);
+                    const int lcol = NT == 2 ? 8 * (lane >> 4) : 0;
+                    for (int kbi = grp; kbi < nkb; kbi += groups) {
+                        const int c0 = kbi * 16 + 2 * t4;
+                        const int cs[4] = {c0, c0 + 1, c0 + 8, c0 + 9};
+                        float kh[8], kl[8];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 yh = sy[cs[u]], yl = sy[kOzTileCap + cs[u]];
+                            oz_entry<KID, D>(x0h, x0l, yh, yl, kh[u], kl[u]);
+                            oz_entry<KID, D>(x1h, x1l, yh, yl, kh[4 + u], kl[4 + u]);
+                        }
+                        uint32_t B[kOzDigits][NT][2];
+                        const uint32_t rowaddr = sd_base + (uint32_t)((kbi * 16 + lrow) * Lay::kStride) + 2u * lcol;
+#pragma unroll
+                        for (int t = 0; t < kOzDigits; ++t) {
+                            const uint32_t ad = rowaddr + (uint32_t)(t * NC * 2);
+                            if (NT == 2)
+                                oz_ldsm_x4_trans(ad, B[t][0][0], B[t][0][1], B[t][NT - 1][0], B[t][NT - 1][1]);
+                            else
+                                oz_ldsm_x2_trans(ad, B[t][0][0], B[t][0][1]);
+                        }
+                        // digits of the 8 entries, most significant first, each
+                        // multiplied at once with the vector digits of the levels it reaches
+                        float r[8];
+#pragma unroll
+                        for (int s = 0; s < kOzDigits; ++s) {
+                            float dg[8];
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) {
+                                if (s == 0) {
+                                    dg[v] = fmaf(kh[v], sc0[v >> 2], kOzShift) - kOzShift;
+                                    r[v] = fmaf(kh[v], sc0[v >> 2], -dg[v]);
+                                } else if (s == 3) {
+                                    const float x = fmaf(r[v], 256.0f, kl[v] * (sc0[v >> 2] * 16777216.0f));
+                                    dg[v] = (x + kOzShift) - kOzShift;
+                                    r[v] = x - dg[v];
+                                } else {
+                                    dg[v] = fmaf(r[v], 256.0f, kOzShift) - kOzShift;
+                                    r[v] = fmaf(r[v], 256.0f, -dg[v]);
+                                }
+                            }
+                            const uint32_t a0 = oz_pack(dg[0], dg[1]), a1 = oz_pack(dg[4], dg[5]);
+                            const uint32_t a2 = oz_pack(dg[2], dg[3]), a3 = oz_pack(dg[6], dg[7]);
+#pragma unroll
+                            for (int t = 0; t + s < kOzDigits; ++t)
+#pragma unroll
+                                for (int n = 0; n < NT; ++n) oz_mma(C[s + t][n], a0, a1, a2, a3, B[t][n][0], B[t][n][1]);
+                        }
+                    }
+                    // flush: sum_L C_L 2^-8L, scaled to the column's reference
+                    // exponent, into the double-float accumulators
+#pragma unroll
+                    for (int n = 0; n < NT; ++n)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int o = n * 4 + c;
+                            const float fac = ldexpf(1.0f, sfd[lv * 16 + oz_col(o)]);
+                            const float tail =
+                                fmaf(C[5][n][c], 1.0f / 65536.0f, fmaf(C[4][n][c], 1.0f / 256.0f, C[3][n][c]));
+                            float h, l, e2, e3;
+                            two_sum_ordered(C[0][n][c], C[1][n][c] * (1.0f / 256.0f), h, l);
+                            two_sum_ordered(h, C[2][n][c] * (1.0f / 65536.0f), h, e2);
+                            l = fmaf(tail, 1.0f / 16777216.0f, l + e2);
+                            float ah = acc[(2 * o) * kOzThreads + tid], al = acc[(2 * o + 1) * kOzThreads + tid];
+                            two_sum_ordered(ah, h * fac, ah, e3);
+                            al = al + (e3 + l * fac);
+                            fast_two_sum(ah, al, ah, al);
+                            acc[(2 * o) * kOzThreads + tid] = ah;
+                            acc[(2 * o + 1) * kOzThreads + tid] = al;
+#pragma unroll
+                            for (int L = 0; L < kOzDigits; ++L) C[L][n][c] = 0.f;
+                        }
+                }
+                __syncthreads();
+                pos += fill;
+            }
+        }
+        // reduce the source groups in a fixed order, then scale and write
+        for (int gg = 0; gg < groups; ++gg) {
+            if (active && grp == gg) {
+#pragma unroll
+                for (int o = 0; o < NT * 4; ++o) {
+                    const int row = (o & 3) < 2 ? r0 : r1;
+                    const double v =
+                        (double)acc[(2 * o) * kOzThreads + tid] + (double)acc[(2 * o + 1) * kOzThreads + tid];
+                    double *dst = red + row * NC + oz_col(o);
+                    *dst = gg == 0 ? v : *dst + v;
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < tcount * ldq; q += kOzThreads) {
+            const int row = q / ldq, c = q - row * ldq;
+            a.out[(toff + tb) * ldq + q] = red[row * NC + c] * ldexp(a.scale, rowE[row] - 16) * a.colscale[c];
+        }
+        __syncthreads();
+    }
+}
+
+template <int KID, int D, int NT>
+static void launch_oz(const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
+    const size_t smem = OzLayout<8 * NT>::kBytes;
+    auto kern = ksum_oz_kernel<KID, D, NT>;
+    allow_max_dynamic_smem((const void *)kern);
+    kern<<<(unsigned)ntn, kOzThreads, smem, s>>>(a);
+    LAUNCHED();
+}
+
+template <int KID, int D>
+static void launch_oz_nt(const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
+    if (a.ldq <= 8)
+        launch_oz<KID, D, 1>(a, ntn, s);
+    else
+        launch_oz<KID, D, 2>(a, ntn, s);
+}
+
+bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq) {
+    return !dd_exact_coupling(h) && ldq <= 16 && h->tau < 1.0 && h->L < kOzLevels &&
+           (kid == SMASH_K_INVR || kid == SMASH_K_CAUCHY1D) && h->nnodes > h->nroots;
+}
+
+void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s) {
+    const Side &R = h->row;
+    const Side &Cs = *h->col;
+    const int NC = ldq <= 8 ? 8 : 16;
+    const int64_t nsk = std::max<int64_t>(Cs.total_skel, 1);
+    Arena tmp(s);
+    unsigned long long *cmax = tmp.alloc<unsigned long long>(kOzLevels * 16);
+    int *fd = tmp.alloc<int>(kOzLevels * 16);
+    int *fref = tmp.alloc<int>(16);
+    double *colscale = tmp.alloc<double>(16);
+    __nv_bfloat16 *dig = tmp.alloc<__nv_bfloat16>((size_t)nsk * kOzDigits * NC);
+    CK(cudaMemsetAsync(cmax, 0, kOzLevels * 16 * sizeof(unsigned long long), s));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((h->nnodes + 7) / 8, 8 * (int64_t)h->num_sms));
+    oz_colmax_kernel<<<blocks, 256, 0, s>>>(qhat, ldq, h->nnodes, h->level, Cs.k, Cs.sk_off, cmax);
+    LAUNCHED();
+    oz_scales_kernel<<<1, 32, 0, s>>>(cmax, fd, fref, colscale);
+    LAUNCHED();
+    oz_digits_kernel<<<blocks, 256, 0, s>>>(qhat, ldq, NC, h->nnodes, h->level, Cs.k, Cs.sk_off, fd, fref, dig);
+    LAUNCHED();
+    KsumOzArgs a{};
+    a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
+    a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
+    a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.dig = dig; a.fd = fd; a.colscale = colscale;
+    a.level = h->level; a.cell = h->cell; a.out = zhat; a.scale = 1.0 / h->s; a.ldq = ldq; a.dim = h->dim;
+    const int64_t ntn = h->nnodes - h->nroots;
+    if (kid == SMASH_K_CAUCHY1D)
+        launch_oz_nt<SMASH_K_CAUCHY1D, 1>(a, ntn, s);
+    else if (h->dim == 3)
+        launch_oz_nt<SMASH_K_INVR, 3>(a, ntn, s);
+    else if (h->dim == 2)
+        launch_oz_nt<SMASH_K_INVR, 2>(a, ntn, s);
+    else
+        launch_oz_nt<SMASH_K_INVR, 1>(a, ntn, s);
+    tmp.release();
+}
+
+}  // namespace smash

@@ -1,0 +1,147 @@
+"""GPU parity of the coupling with exact digit-split products on the tensor cores.
+
+The double-float matvec (SMASH_PREC_F32X2) computes the coupling (3.19) in one
+of two ways, chosen per launch shape by the tuner (default: the first):
+  0. entries in double-float, entries and q^ split into 8-bit digits whose
+     products are summed exactly on the tensor cores, the digit levels
+     combined in double-float;
+  1. every operation in double-float on the FP32 pipe.
+Both carry ~2^-46 relative precision per entry, so both meet the FP64 bar
+(1e-11 relative 2-norm against the oracle's FP64 H^2 matvec) and agree with
+each other far below it.  Blocks the digit split does not cover (more than
+16 right-hand sides per pass; trees on the exact three-float coordinates)
+take the second way.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import smash_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1705_05443_gb300 as sm  # noqa: E402
+
+DEV = torch.device("cuda:0")
+F32X2 = sm.SMASH_PREC_F32X2
+RTOL = 1e-11
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture
+def clean_table():
+    sm.smash_set_autotune(False)
+    sm.smash_autotune_clear()
+    yield
+    sm.smash_set_autotune(False)
+    sm.smash_autotune_clear()
+
+
+def _coupling_keys(h, q, tmp_path):
+    sm.smash_set_autotune(True)
+    h.matvec(_dev(q), precision=F32X2)
+    sm.smash_set_autotune(False)
+    path = tmp_path / "t.json"
+    sm.smash_autotune_save(str(path))
+    table = json.loads(path.read_text())["entries"]
+    return table, [k for k in table if k.startswith("coupling_dd/")], path
+
+
+def _forced(h, q, table, keys, path, choice):
+    forced = dict(table)
+    forced.update({k: choice for k in keys})
+    path.write_text(json.dumps({"smash_autotune": 1, "entries": forced}))
+    sm.smash_autotune_clear()
+    sm.smash_autotune_load(str(path))
+    return h.matvec(_dev(q), precision=F32X2).cpu().numpy()
+
+
+@pytest.mark.parametrize("d,n,leaf,order,nrhs", [(3, 20000, 128, 4, 16), (3, 9000, 64, 3, 5), (2, 8000, 64, 5, 8),
+                                                 (2, 6000, 32, 6, 16), (1, 4000, 32, 10, 1), (1, 5000, 64, 8, 12)])
+def test_both_couplings_match_the_oracle(clean_table, tmp_path, d, n, leaf, order, nrhs):
+    x = si.uniform_cube(n, d, 6100 + d)
+    q = si.rhs(n, nrhs, 6101)
+    zo = oracle.H2(x, sm.SMASH_K_INVR, leaf, order, 1e-8).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, leaf, order, 1e-8)
+    table, keys, path = _coupling_keys(h, q, tmp_path)
+    assert keys, "the digit-split coupling is offered for this tree"
+    z0 = _forced(h, q, table, keys, path, 0)
+    z1 = _forced(h, q, table, keys, path, 1)
+    assert _rel(z0, zo) <= RTOL
+    assert _rel(z1, zo) <= RTOL
+    # the two ways differ only by roundings of the double-float arithmetic
+    assert _rel(z0, z1) <= 1e-12
+    h.close()
+
+
+def test_default_matvec_takes_the_digit_split_coupling(clean_table):
+    """With tuning off and an empty table the default (0) is used; the result
+    is deterministic (fixed reduction order) and meets the bar."""
+    x = si.sphere_with_caps(12000, 6200)
+    q = si.rhs(12000, 16, 6201)
+    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
+    za = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    zb = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    assert np.array_equal(za, zb)
+    assert _rel(za, zo) <= RTOL
+    h.close()
+
+
+def test_cauchy_rectangular_digit_split(clean_table, tmp_path):
+    x, y = si.cauchy_1d(6000, 6300)
+    q = si.rhs(6000, 4, 6301)
+    zo = oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=_dev(y))
+    table, keys, path = _coupling_keys(h, q, tmp_path)
+    assert keys
+    for choice in (0, 1):
+        assert _rel(_forced(h, q, table, keys, path, choice), zo) <= RTOL, choice
+    h.close()
+
+
+def test_wide_scales_of_q_columns(clean_table, tmp_path):
+    """Columns scaled by 2^-40 .. 2^40 and a zero column: every column keeps
+    its own exponent, so each meets the bar on its own."""
+    x = si.uniform_cube(10000, 3, 6400)
+    q = si.rhs(10000, 8, 6401)
+    q = q * (2.0 ** np.array([-40, -13, 0, 7, 19, 40, 0, 3]))[None, :]
+    q[:, 6] = 0.0
+    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
+    table, keys, path = _coupling_keys(h, q, tmp_path)
+    z = _forced(h, q, table, keys, path, 0)
+    for c in range(8):
+        if c == 6:
+            assert not np.any(z[:, c])
+        else:
+            assert _rel(z[:, c], zo[:, c]) <= RTOL, c
+    h.close()
+
+
+@pytest.mark.parametrize("nrhs", [17, 40])
+def test_wide_blocks_take_the_double_float_coupling(clean_table, tmp_path, nrhs):
+    """More than 16 right-hand sides exceed one pass of the digit-split
+    kernel: no digit-split key is offered and the double-float coupling meets
+    the bar."""
+    x = si.uniform_cube(8000, 3, 6500)
+    q = si.rhs(8000, nrhs, 6501)
+    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
+    _, keys, _ = _coupling_keys(h, q, tmp_path)
+    assert not keys
+    assert _rel(h.matvec(_dev(q), precision=F32X2).cpu().numpy(), zo) <= RTOL
+    h.close()
