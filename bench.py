@@ -45,6 +45,28 @@ DD_MAC_OPS = 12            # double-float: FP32 instructions of one error-free m
 # scaled to other sizes by the entries of the launch
 DD_COUPLING_TRAFFIC = (53.189376e6 + 13.053952e6, 6099084090)
 F32_EVAL_OPS = 14          # FP32: two-float difference (9), squared distance (3), rsqrt + select (2)
+# digit-split coupling: FP32-pipe instructions per entry -- the double-float
+# 1/|x-y| of an admissible pair (43) and its split into six digits with their
+# packing to bf16 (23); the 21 digit products per entry and column run on the
+# tensor cores (mma.sync m16n8k16) and are not counted
+OZ_EVAL_OPS = 43 + 23
+OZ_PRODUCTS = 21
+# DRAM bytes of one digit-split coupling launch (3D 1/r, N = 2^18, 16 RHS,
+# 6.099e9 entries) from ncu (profiles/ksum_oz_coupling_3d_invr_262144.md)
+OZ_COUPLING_TRAFFIC = (73.66784e6 + 21.727744e6, 6099084090)
+
+
+def _coupling_choice(sm):
+    """Which double-float coupling the tuner recorded (0 digit split on the
+    tensor cores, 1 all on the FP32 pipe), or None when nothing is recorded."""
+    import json
+    import tempfile
+    with tempfile.NamedTemporaryFile(suffix=".json") as f:
+        if sm.smash_autotune_save(f.name) != 0:
+            return None
+        entries = json.load(open(f.name)).get("entries", {})
+    vals = [v for k, v in entries.items() if k.startswith("coupling_dd/")]
+    return vals[0] if vals else None
 
 
 def _dist():
@@ -547,6 +569,15 @@ def bench_ours(args, w):
         psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
                 "(one FMA = one operation)")
         wdef = f"per kernel entry nrhs FMAs + {F32_EVAL_OPS} FP32 instructions (difference, distance, kernel)"
+    elif (_coupling_choice(sm) or 0) == 0 and nrhs <= 16 and info["levels"] <= 10:
+        peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        cpl_work = info["coupling_pairs"] * OZ_EVAL_OPS
+        kname = ("coupling (ksum_oz_kernel over L: double-float entries split into 8-bit digits on the FP32 "
+                 "pipe, exact digit products on the tensor cores)")
+        psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
+                "(one FMA = one operation)")
+        wdef = (f"per kernel entry {OZ_EVAL_OPS} FP32-pipe instructions (double-float 1/|x-y| and its six-digit "
+                f"split); the {OZ_PRODUCTS}*nrhs digit products per entry run as mma.sync and are not counted")
     else:
         peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         cpl_work = info["coupling_pairs"] * (DD_MAC_OPS * nrhs + DD_EVAL_OPS)
@@ -558,7 +589,8 @@ def bench_ours(args, w):
     achieved = cpl_work / (cpl_ms / 1e3) / 1e12
     traffic = None
     if prec == sm.SMASH_PREC_F32X2 and args.workload == "3d_invr_1m":
-        traffic = DD_COUPLING_TRAFFIC[0] * info["coupling_pairs"] / DD_COUPLING_TRAFFIC[1]
+        tr = DD_COUPLING_TRAFFIC if kname.startswith("coupling (ksum_dd") else OZ_COUPLING_TRAFFIC
+        traffic = tr[0] * info["coupling_pairs"] / tr[1]
     mixed = run_mixed(sm, torch, dev) if args.mixed else None
     batched = None
     if args.batched:
