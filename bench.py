@@ -56,9 +56,10 @@ OZ_PRODUCTS = 21
 OZ_COUPLING_TRAFFIC = (73.66784e6 + 21.727744e6, 6099084090)
 
 
-def _coupling_choice(sm):
-    """Which double-float coupling the tuner recorded (0 digit split on the
-    tensor cores, 1 all on the FP32 pipe), or None when nothing is recorded."""
+def _coupling_choice(sm, nrhs):
+    """Which double-float coupling ran: the tuner's record (0 digit split on
+    the tensor cores, 1 all on the FP32 pipe), else the untuned default (the
+    digit split from 8 columns per pass)."""
     import json
     import tempfile
     with tempfile.NamedTemporaryFile(suffix=".json") as f:
@@ -66,7 +67,10 @@ def _coupling_choice(sm):
             return None
         entries = json.load(open(f.name)).get("entries", {})
     vals = [v for k, v in entries.items() if k.startswith("coupling_dd/")]
-    return vals[0] if vals else None
+    if vals:
+        return vals[0]
+    ldq = 1 << max(0, (nrhs - 1).bit_length()) if nrhs <= 32 else 32 * ((nrhs + 31) // 32)
+    return 0 if ldq >= 8 else 1
 
 
 def _dist():
@@ -569,7 +573,7 @@ def bench_ours(args, w):
         psrc = (f"FP32 pipe {FP32_OPS_PER_CLK_SM} instructions/clk/SM x {NUM_SMS} SMs x {sm_mhz:.0f} MHz "
                 "(one FMA = one operation)")
         wdef = f"per kernel entry nrhs FMAs + {F32_EVAL_OPS} FP32 instructions (difference, distance, kernel)"
-    elif (_coupling_choice(sm) or 0) == 0 and nrhs <= 16 and info["levels"] <= 10:
+    elif _coupling_choice(sm, nrhs) == 0 and nrhs <= 16 and info["levels"] <= 10:
         peak = NUM_SMS * FP32_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         cpl_work = info["coupling_pairs"] * OZ_EVAL_OPS
         kname = ("coupling (ksum_oz_kernel over L: double-float entries split into 8-bit digits on the FP32 "

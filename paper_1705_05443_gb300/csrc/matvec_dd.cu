@@ -379,7 +379,10 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
     tm.mark();
     // the coupling: products on the tensor cores (exact digit splits) where
     // the tree allows it, else every operation in double-float on the FP32
-    // pipe; the tuner may take either
+    // pipe; the tuner may take either.  Untuned, the digit split is the
+    // default from 8 columns per pass: its entry and digit work (~90
+    // instructions per entry) is fixed, while the FP32-pipe products cost 12
+    // instructions per column.
     auto dd_coupling = [&] {
         dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
         KsumDDArgs a{};
@@ -396,7 +399,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
             char key[128];
             std::snprintf(key, sizeof(key), "coupling_dd/sm%d/k%d/d%d/ld%d/n%lld", h->num_sms, kid, h->dim, ldq,
                           pow2_at_least(h->nnodes));
-            tune_choose(key, {0, 1}, 0, s, [&](int c) {
+            tune_choose(key, {0, 1}, ldq >= 8 ? 0 : 1, s, [&](int c) {
                 if (c == 0) coupling_oz(h, kid, qhat, zhat, ldq, s);
                 else dd_coupling();
             });

@@ -1,7 +1,8 @@
 """GPU parity of the coupling with exact digit-split products on the tensor cores.
 
 The double-float matvec (SMASH_PREC_F32X2) computes the coupling (3.19) in one
-of two ways, chosen per launch shape by the tuner (default: the first):
+of two ways, chosen per launch shape by the tuner (untuned default: the first
+from 8 columns per pass, else the second):
   0. entries in double-float, entries and q^ split into 8-bit digits whose
      products are summed exactly on the tensor cores, the digit levels
      combined in double-float;
