@@ -50,8 +50,8 @@ namespace smash {
 
 constexpr int kOzDigits = 6;
 constexpr int kOzThreads = 256;
-constexpr int kOzTileCap = 256;  // sources per tile (two or more warps per row tile)
-constexpr int kOzRows = 128;     // targets per pass (8 row tiles of 16)
+constexpr int kOzTileCap = 224;  // sources per tile when two or more warps share a target tile
+constexpr int kOzRows = 64;      // targets per pass (8 target tiles of 8)
 
 // ------------------------------------------------------------------ q^ digits
 constexpr int kOzLevels = 16;  // rows of the per-level tables (levels 0..10 on this path)
@@ -193,7 +193,8 @@ struct KsumOzArgs {
 };
 
 // digit bytes per source in shared memory: 6 * NC bf16 plus 16 bytes of pad,
-// which puts the 8 rows of an ldmatrix on distinct banks
+// which puts the 8 rows of an ldmatrix on distinct banks.  The group
+// reduction at the end of a pass reuses the digit region.
 template <int NC>
 struct OzLayout {
     static constexpr int kDigitBytes = kOzDigits * NC * 2;
@@ -202,8 +203,9 @@ struct OzLayout {
     static constexpr size_t kDigits = (size_t)kStride * kOzTileCap;
     static constexpr size_t kIdx = sizeof(int64_t) * kOzTileCap;
     static constexpr size_t kRed = sizeof(double) * kOzRows * NC;
-    static constexpr size_t kAcc = sizeof(float) * 2 * (NC / 2) * kOzThreads;  // (hi, lo) per output per thread
-    static constexpr size_t kBytes = kCoords + kDigits + kIdx + kRed + kAcc;
+    static constexpr size_t kAcc = sizeof(float) * 2 * 4 * kOzThreads;  // (hi, lo) of 4 outputs per thread
+    static constexpr size_t kBytes = kCoords + kDigits + kIdx + kAcc;
+    static_assert(kRed <= kDigits, "the group reduction fits the digit region");
 };
 
 // bound of target node g's row from the cells alone: max over partners j of
@@ -321,8 +323,14 @@ __device__ __forceinline__ void oz_entry(const float4 &xh, const float4 &xl, con
         oz_invr<D>(dh, dl, kh, kl);
 }
 
+// One CTA per target node.  mma.sync m16n8k16 with the roles
+//   M = 16 right-hand sides (q^ digits, A operand, ldmatrix from the staged tile),
+//   N = 8 targets (entry digits, B operand, evaluated in registers),
+//   K = 16 sources,
+// so a warp owns 8 targets, each lane evaluates the 4 entries of its target
+// and 4 sources of a k-block, and the six level sums take 24 registers.
 template <int KID, int D, int NT>
-__global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
+__global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
     constexpr int NC = 8 * NT;
     using Lay = OzLayout<NC>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -332,12 +340,12 @@ __global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
     __shared__ int plev[kPartnerChunk];
     __shared__ int sfd[kOzLevels * 16];
     __shared__ int rowE[kOzRows];
-    float4 *sy = reinterpret_cast<float4 *>(smraw);                           // [2][cap]: hi, lo
-    unsigned char *sd = smraw + Lay::kCoords;                                 // [cap][stride]
-    int64_t *sidx = reinterpret_cast<int64_t *>(sd + Lay::kDigits);           // [cap]
-    double *red = reinterpret_cast<double *>(smraw + Lay::kCoords + Lay::kDigits + Lay::kIdx);  // [rows][NC]
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // [2][cap]: hi, lo
+    unsigned char *sd = smraw + Lay::kCoords;                        // [cap][stride]
+    int64_t *sidx = reinterpret_cast<int64_t *>(sd + Lay::kDigits);  // [cap]
     // running double-float sums, touched once per tile: [2 * output + (0 hi, 1 lo)][thread]
-    float *acc = reinterpret_cast<float *>(smraw + Lay::kCoords + Lay::kDigits + Lay::kIdx + Lay::kRed);
+    float *acc = reinterpret_cast<float *>(smraw + Lay::kCoords + Lay::kDigits + Lay::kIdx);
+    double *red = reinterpret_cast<double *>(sd);  // [rows][NC], after the last tile of a pass
 
     const int64_t g = a.tnodes[blockIdx.x];
     const int T = a.t_cnt[g];
@@ -356,47 +364,40 @@ __global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
         for (int q = tid; q < T * ldq; q += kOzThreads) a.out[toff * ldq + q] = NAN;
         return;
     }
+    // ldmatrix rows of the q^ digits: lane l addresses source
+    // kb*16 + (l & 7) + 8 (source half), columns 8 (right-hand-side half)
+    const int lsrc = (lane & 7) + 8 * (NT == 2 ? (lane >> 4) : ((lane >> 3) & 1));
+    const int lrhs = NT == 2 ? 8 * ((lane >> 3) & 1) : 0;
 
     for (int tb = 0; tb < T; tb += kOzRows) {
         const int tcount = min(kOzRows, T - tb);
-        const int wr = (tcount + 15) / 16;  // row tiles
-        const int groups = 8 / wr;          // warps along the sources per row tile
+        const int wr = (tcount + 7) / 8;  // target tiles
+        const int groups = 8 / wr;        // warps along the sources per target tile
         const int grp = warp / wr, rt = warp % wr;
         const bool active = grp < groups;
-        const int tile = groups == 1 ? kOzTileCap / 2 : kOzTileCap;  // <= 128 sources per warp per flush
-        const int r0 = rt * 16 + gq, r1 = r0 + 8;
-        // rows past the block take row 0's point (finite entries, discarded)
-        const int rr0 = r0 < tcount ? r0 : 0, rr1 = r1 < tcount ? r1 : 0;
-        const float4 *p0 = reinterpret_cast<const float4 *>(a.xt + (toff + tb + rr0) * 8);
-        const float4 *p1 = reinterpret_cast<const float4 *>(a.xt + (toff + tb + rr1) * 8);
-        const float4 x0h = p0[0], x0l = p0[1], x1h = p1[0], x1l = p1[1];
-        // row exponents of the thread's two targets
-        float sc0[2];  // first digit: K 2^(8-E); lo(K) enters the fourth digit at 2^24 times that
+        const int tile = groups == 1 ? 128 : kOzTileCap;  // <= 128 sources per warp per flush
+        // the lane's target; targets past the block take target 0's point (finite entries, discarded)
+        const int tr = rt * 8 + gq;
+        const float4 *px = reinterpret_cast<const float4 *>(a.xt + (toff + tb + (tr < tcount ? tr : 0)) * 8);
+        const float4 xh = px[0], xl = px[1];
+        // first digit: K 2^(8-E); lo(K) enters the fourth digit at 2^24 times that
+        float sc0;
         {
-            const int E0 = oz_row_exponent(oz_point_gap2<D>(x0h, a, e0, e1, t4), kb_node);
-            const int E1 = oz_row_exponent(oz_point_gap2<D>(x1h, a, e0, e1, t4), kb_node);
-            sc0[0] = ldexpf(1.0f, 8 - E0);
-            sc0[1] = ldexpf(1.0f, 8 - E1);
-            if (active && grp == 0 && t4 == 0) {
-                rowE[r0] = E0;
-                rowE[r1] = E1;
-            }
+            const int E = oz_row_exponent(oz_point_gap2<D>(xh, a, e0, e1, t4), kb_node);
+            sc0 = ldexpf(1.0f, 8 - E);
+            if (active && grp == 0 && t4 == 0) rowE[tr] = E;
         }
-        // output o = 4 n + c of the thread: row r0 (c < 2) or r1, column oz_col(o)
-        auto oz_col = [t4](int o) { return (o >> 2) * 8 + 2 * t4 + (o & 1); };
-
+        // output o of the lane: right-hand side gq + 8 (o >> 1), target rt * 8 + 2 t4 + (o & 1)
 #pragma unroll
-        for (int o = 0; o < NT * 4; ++o) {
+        for (int o = 0; o < 4; ++o) {
             acc[(2 * o) * kOzThreads + tid] = 0.f;
             acc[(2 * o + 1) * kOzThreads + tid] = 0.f;
         }
-        float C[kOzDigits][NT][4];
+        float C[kOzDigits][4];
 #pragma unroll
         for (int L = 0; L < kOzDigits; ++L)
 #pragma unroll
-            for (int n = 0; n < NT; ++n)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) C[L][n][c] = 0.f;
+            for (int c = 0; c < 4; ++c) C[L][c] = 0.f;
 
         for (int64_t e = e0; e < e1;) {
             load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
@@ -446,43 +447,40 @@ __global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
                 __syncthreads();
                 if (active) {
                     const uint32_t sd_base = (uint32_t)__cvta_generic_to_shared(sd);
-                    // ldmatrix rows: lane l addresses source kb*16 + (l & 7) + 8 ((l >> 3) & 1),
-                    // columns 8 (l >> 4) of each digit plane
-                    const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1);
-                    const int lcol = NT == 2 ? 8 * (lane >> 4) : 0;
                     for (int kbi = grp; kbi < nkb; kbi += groups) {
                         const int c0 = kbi * 16 + 2 * t4;
                         const int cs[4] = {c0, c0 + 1, c0 + 8, c0 + 9};
-                        float kh[8], kl[8];
+                        float kh[4], kl[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float4 yh = sy[cs[u]], yl = sy[kOzTileCap + cs[u]];
-                            oz_entry<KID, D>(x0h, x0l, yh, yl, kh[u], kl[u]);
-                            oz_entry<KID, D>(x1h, x1l, yh, yl, kh[4 + u], kl[4 + u]);
-                        }
-                        uint32_t B[kOzDigits][NT][2];
-                        const uint32_t rowaddr = sd_base + (uint32_t)((kbi * 16 + lrow) * Lay::kStride) + 2u * lcol;
+                        for (int u = 0; u < 4; ++u)
+                            oz_entry<KID, D>(xh, xl, sy[cs[u]], sy[kOzTileCap + cs[u]], kh[u], kl[u]);
+                        // q^ digits of the k-block: A fragments of the six planes
+                        uint32_t A[kOzDigits][4];
+                        const uint32_t rowaddr = sd_base + (uint32_t)((kbi * 16 + lsrc) * Lay::kStride) + 2u * lrhs;
 #pragma unroll
                         for (int t = 0; t < kOzDigits; ++t) {
                             const uint32_t ad = rowaddr + (uint32_t)(t * NC * 2);
-                            if (NT == 2)
-                                oz_ldsm_x4_trans(ad, B[t][0][0], B[t][0][1], B[t][NT - 1][0], B[t][NT - 1][1]);
-                            else
-                                oz_ldsm_x2_trans(ad, B[t][0][0], B[t][0][1]);
+                            if (NT == 2) {
+                                oz_ldsm_x4_trans(ad, A[t][0], A[t][1], A[t][2], A[t][3]);
+                            } else {
+                                oz_ldsm_x2_trans(ad, A[t][0], A[t][2]);
+                                A[t][1] = 0u;
+                                A[t][3] = 0u;
+                            }
                         }
-                        // digits of the 8 entries, most significant first, each
+                        // digits of the 4 entries, most significant first, each
                         // multiplied at once with the vector digits of the levels it reaches
-                        float r[8];
+                        float r[4];
 #pragma unroll
                         for (int s = 0; s < kOzDigits; ++s) {
-                            float dg[8];
+                            float dg[4];
 #pragma unroll
-                            for (int v = 0; v < 8; ++v) {
+                            for (int v = 0; v < 4; ++v) {
                                 if (s == 0) {
-                                    dg[v] = fmaf(kh[v], sc0[v >> 2], kOzShift) - kOzShift;
-                                    r[v] = fmaf(kh[v], sc0[v >> 2], -dg[v]);
+                                    dg[v] = fmaf(kh[v], sc0, kOzShift) - kOzShift;
+                                    r[v] = fmaf(kh[v], sc0, -dg[v]);
                                 } else if (s == 3) {
-                                    const float x = fmaf(r[v], 256.0f, kl[v] * (sc0[v >> 2] * 16777216.0f));
+                                    const float x = fmaf(r[v], 256.0f, kl[v] * (sc0 * 16777216.0f));
                                     dg[v] = (x + kOzShift) - kOzShift;
                                     r[v] = x - dg[v];
                                 } else {
@@ -490,52 +488,49 @@ __global__ void __launch_bounds__(kOzThreads, 2) ksum_oz_kernel(KsumOzArgs a) {
                                     r[v] = fmaf(r[v], 256.0f, -dg[v]);
                                 }
                             }
-                            const uint32_t a0 = oz_pack(dg[0], dg[1]), a1 = oz_pack(dg[4], dg[5]);
-                            const uint32_t a2 = oz_pack(dg[2], dg[3]), a3 = oz_pack(dg[6], dg[7]);
+                            const uint32_t b0 = oz_pack(dg[0], dg[1]), b1 = oz_pack(dg[2], dg[3]);
 #pragma unroll
                             for (int t = 0; t + s < kOzDigits; ++t)
-#pragma unroll
-                                for (int n = 0; n < NT; ++n) oz_mma(C[s + t][n], a0, a1, a2, a3, B[t][n][0], B[t][n][1]);
+                                oz_mma(C[s + t], A[t][0], A[t][1], A[t][2], A[t][3], b0, b1);
                         }
                     }
                     // flush: sum_L C_L 2^-8L, scaled to the column's reference
                     // exponent, into the double-float accumulators
 #pragma unroll
-                    for (int n = 0; n < NT; ++n)
+                    for (int o = 0; o < 4; ++o) {
+                        const float fac = ldexpf(1.0f, sfd[lv * 16 + gq + 8 * (o >> 1)]);
+                        const float tail = fmaf(C[5][o], 1.0f / 65536.0f, fmaf(C[4][o], 1.0f / 256.0f, C[3][o]));
+                        float h, l, e2, e3;
+                        two_sum_ordered(C[0][o], C[1][o] * (1.0f / 256.0f), h, l);
+                        two_sum_ordered(h, C[2][o] * (1.0f / 65536.0f), h, e2);
+                        l = fmaf(tail, 1.0f / 16777216.0f, l + e2);
+                        float ah = acc[(2 * o) * kOzThreads + tid], al = acc[(2 * o + 1) * kOzThreads + tid];
+                        two_sum_ordered(ah, h * fac, ah, e3);
+                        al = al + (e3 + l * fac);
+                        fast_two_sum(ah, al, ah, al);
+                        acc[(2 * o) * kOzThreads + tid] = ah;
+                        acc[(2 * o + 1) * kOzThreads + tid] = al;
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int o = n * 4 + c;
-                            const float fac = ldexpf(1.0f, sfd[lv * 16 + oz_col(o)]);
-                            const float tail =
-                                fmaf(C[5][n][c], 1.0f / 65536.0f, fmaf(C[4][n][c], 1.0f / 256.0f, C[3][n][c]));
-                            float h, l, e2, e3;
-                            two_sum_ordered(C[0][n][c], C[1][n][c] * (1.0f / 256.0f), h, l);
-                            two_sum_ordered(h, C[2][n][c] * (1.0f / 65536.0f), h, e2);
-                            l = fmaf(tail, 1.0f / 16777216.0f, l + e2);
-                            float ah = acc[(2 * o) * kOzThreads + tid], al = acc[(2 * o + 1) * kOzThreads + tid];
-                            two_sum_ordered(ah, h * fac, ah, e3);
-                            al = al + (e3 + l * fac);
-                            fast_two_sum(ah, al, ah, al);
-                            acc[(2 * o) * kOzThreads + tid] = ah;
-                            acc[(2 * o + 1) * kOzThreads + tid] = al;
-#pragma unroll
-                            for (int L = 0; L < kOzDigits; ++L) C[L][n][c] = 0.f;
-                        }
+                        for (int L = 0; L < kOzDigits; ++L) C[L][o] = 0.f;
+                    }
                 }
                 __syncthreads();
                 pos += fill;
             }
         }
-        // reduce the source groups in a fixed order, then scale and write
+        // reduce the source groups in a fixed order (red reuses the digit
+        // region: every tile of the pass is done), then scale and write
         for (int gg = 0; gg < groups; ++gg) {
             if (active && grp == gg) {
 #pragma unroll
-                for (int o = 0; o < NT * 4; ++o) {
-                    const int row = (o & 3) < 2 ? r0 : r1;
-                    const double v =
-                        (double)acc[(2 * o) * kOzThreads + tid] + (double)acc[(2 * o + 1) * kOzThreads + tid];
-                    double *dst = red + row * NC + oz_col(o);
-                    *dst = gg == 0 ? v : *dst + v;
+                for (int o = 0; o < 4; ++o) {
+                    const int c = gq + 8 * (o >> 1);
+                    if (c < NC) {
+                        const double v =
+                            (double)acc[(2 * o) * kOzThreads + tid] + (double)acc[(2 * o + 1) * kOzThreads + tid];
+                        double *dst = red + (rt * 8 + 2 * t4 + (o & 1)) * NC + c;
+                        *dst = gg == 0 ? v : *dst + v;
+                    }
                 }
             }
             __syncthreads();
