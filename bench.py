@@ -53,7 +53,7 @@ OZ_EVAL_OPS = 43 + 23
 OZ_PRODUCTS = 21
 # DRAM bytes of one digit-split coupling launch (3D 1/r, N = 2^18, 16 RHS,
 # 6.099e9 entries) from ncu (profiles/ksum_oz_coupling_3d_invr_262144.md)
-OZ_COUPLING_TRAFFIC = (73.66784e6 + 21.727744e6, 6099084090)
+OZ_COUPLING_TRAFFIC = (73.347328e6 + 21.123072e6, 6099084090)
 
 
 def _coupling_choice(sm, nrhs):
@@ -63,9 +63,9 @@ def _coupling_choice(sm, nrhs):
     import json
     import tempfile
     with tempfile.NamedTemporaryFile(suffix=".json") as f:
-        if sm.smash_autotune_save(f.name) != 0:
-            return None
-        entries = json.load(open(f.name)).get("entries", {})
+        sm.smash_autotune_save(f.name)  # raises on failure
+        with open(f.name) as fh:
+            entries = json.load(fh).get("entries", {})
     vals = [v for k, v in entries.items() if k.startswith("coupling_dd/")]
     if vals:
         return vals[0]
