@@ -14,17 +14,20 @@
 //    cell centres c and half-diagonals r (tau < 1), and |x - y| is at least the
 //    distance from the target point x to the partner's cell.  With 2^E_x above
 //    twice the smaller of the two bounds over the row of x, K' = K 2^-E_x lies
-//    in (-1/2, 1/2) and is split as K' = sum_{s<6} a_s 2^{-8(s+1)} with integers
-//    |a_s| <= 128 (round-to-nearest digits; the first three from hi(K), the
-//    last three from the rest).
+//    in (-1/2, 1/2) and is split as K' = sum_{s<6} a_s 2^{-8(s+1)} into
+//    round-to-nearest integer digits: the first three from hi(K), the last
+//    three from the rest.  |a_s| <= 128, except the fourth, which also takes
+//    lo(K) (|lo| <= ulp(hi)/2) and stays within 256.
 //  * Vectors.  Per tree level l and column c, 2^F_lc above twice the largest
 //    |q^_jc| of the level's skeletons scales q^ into (-1/2, 1/2);
 //    q' = sum_{t<6} b_t 2^{-8(t+1)}, |b_t| <= 128, in FP64 once.  A row of L
 //    lists its partners by level, so a tile never mixes two levels.
 //  * Products.  K' q' = sum_L 2^{-8L-16} sum_{s+t=L} a_s b_t, truncated at
-//    L <= 5 (dropped terms below 2^-47 relative).  A digit product is at most
-//    2^14 and a level holds at most 6 of them, so 128 sources sum to less
-//    than 2^24: the FP32 accumulation of bf16 x bf16 products
+//    L <= 5 (dropped terms below 2^-47 relative).  A level holds at most 6
+//    digit products per source, at most one of them with the fourth entry
+//    digit: at most 7 * 2^14 per source, so 128 sources sum to less than
+//    2^24, and every digit (<= 256) is exact in bf16: the FP32 accumulation
+//    of bf16 x bf16 products
 //    (mma.sync m16n8k16) is exact for every level.  After each tile (at most
 //    128 sources per warp) the six level sums are combined by error-free
 //    transformations, scaled by 2^(F_lc - max_l F_lc) (exact), into a
