@@ -340,8 +340,166 @@ static void ksum_dd(const smash_h2 *h, int kid, bool exact, KsumDDArgs a, int64_
     tune_choose(key, cands, 0, s, run);
 }
 
-// ------------------------------------------------------------------ transfers (FP64)
-// The upward and downward passes are HBM-bound and stay in FP64.
+// ------------------------------------------------------------------ transfers (double-float)
+// The upward and downward passes of Section 3.4 with the products of G in
+// double-float on the FP32 pipe: 2 nrhs FP64 flops per 8-byte G entry would
+// keep them on the FP64 pipe.  One CTA per node; rows of G are split into
+// (hi, lo) pairs once per CTA in shared memory, kTrRows at a time.
+constexpr int kTrThreads = 256;
+constexpr int kTrRows = 32;
+
+struct PassDDArgs {
+    int64_t n0;
+    const int32_t *leaf, *m, *k;
+    const int64_t *in_off, *sk_off, *loc_off, *g_off;
+    const int32_t *loc;
+    const double *G;
+    const float2 *pts2;  // upward: leaf inputs (sorted points, ldq)
+    float2 *skel2;       // upward: q^ as (hi, lo) (children read, the node written)
+    double *skel64;      // upward: q^ in FP64 (written); downward: z^ (the node read, children +=)
+    double *pts_out;     // downward: zs of the leaves (+=)
+    int ldq;
+};
+
+__device__ __forceinline__ float2 split_f64(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// (sh, sl) += (gh + gl)(x.x + x.y): the product hi * hi exact by FMA, cross
+// terms rounded into the error term, the running sum by error-free Fast2Sum
+__device__ __forceinline__ void dd_mac(float gh, float gl, float2 x, float &sh, float &sl) {
+    const float p = gh * x.x;
+    float pe = fmaf(gh, x.x, -p);
+    pe = fmaf(gh, x.y, pe);
+    pe = fmaf(gl, x.x, pe);
+    float s, t;
+    two_sum_ordered(sh, p, s, t);
+    sh = s;
+    sl = sl + (t + pe);
+}
+
+// q^_i[t] = x[skel_t] + sum_u G[u][t] x[rest_u],  x = q|_i (leaf) or [q^_c] (parent)
+__global__ void __launch_bounds__(kTrThreads) upward_dd_kernel(PassDDArgs a) {
+    extern __shared__ float2 sG[];  // kTrRows x k
+    const int64_t g = a.n0 + blockIdx.x;
+    const int m = a.m[g], k = a.k[g];
+    if (k == 0) return;
+    const int ldq = a.ldq, mk = m - k;
+    const float2 *in = a.leaf[g] ? a.pts2 + a.in_off[g] * ldq : a.skel2 + a.in_off[g] * ldq;
+    const int32_t *loc = a.loc + a.loc_off[g];
+    const double *G = a.G + a.g_off[g];
+    float2 *out2 = a.skel2 + a.sk_off[g] * ldq;
+    double *out64 = a.skel64 + a.sk_off[g] * ldq;
+    const int nout = k * ldq;
+    const int tid = threadIdx.x;
+    for (int b0 = 0; b0 < nout; b0 += 4 * kTrThreads) {
+        float sh[4], sl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = b0 + j * kTrThreads + tid;
+            sh[j] = 0.f;
+            sl[j] = 0.f;
+            if (e < nout) {
+                const float2 x = in[(int64_t)loc[e / ldq] * ldq + e % ldq];
+                sh[j] = x.x;
+                sl[j] = x.y;
+            }
+        }
+        for (int u0 = 0; u0 < mk; u0 += kTrRows) {
+            const int rows = min(kTrRows, mk - u0);
+            __syncthreads();  // the previous rows are consumed
+            for (int q = tid; q < rows * k; q += kTrThreads) sG[q] = split_f64(G[(int64_t)u0 * k + q]);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = b0 + j * kTrThreads + tid;
+                if (e < nout) {
+                    const int t = e / ldq, c = e % ldq;
+                    for (int u = 0; u < rows; ++u) {
+                        const float2 gg = sG[u * k + t];
+                        dd_mac(gg.x, gg.y, in[(int64_t)loc[k + u0 + u] * ldq + c], sh[j], sl[j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = b0 + j * kTrThreads + tid;
+            if (e < nout) {
+                float h, l;
+                fast_two_sum(sh[j], sl[j], h, l);
+                out2[e] = make_float2(h, l);
+                out64[e] = (double)h + (double)l;
+            }
+        }
+    }
+}
+
+// out[skel_t] += z^_i[t];  out[rest_u] += sum_t G[u][t] z^_i[t] (the sum in double-float)
+__global__ void __launch_bounds__(kTrThreads) downward_dd_kernel(PassDDArgs a) {
+    extern __shared__ float2 smem2[];
+    const int64_t g = a.n0 + blockIdx.x;
+    const int m = a.m[g], k = a.k[g];
+    if (k == 0) return;
+    const int ldq = a.ldq, mk = m - k;
+    const double *zin = a.skel64 + a.sk_off[g] * ldq;
+    double *out = a.leaf[g] ? a.pts_out + a.in_off[g] * ldq : a.skel64 + a.in_off[g] * ldq;
+    const int32_t *loc = a.loc + a.loc_off[g];
+    const double *G = a.G + a.g_off[g];
+    float2 *sz = smem2;            // k x ldq
+    float2 *sG = smem2 + k * ldq;  // kTrRows x k
+    const int tid = threadIdx.x;
+    for (int e = tid; e < k * ldq; e += kTrThreads) {
+        const double v = zin[e];
+        sz[e] = split_f64(v);
+        out[(int64_t)loc[e / ldq] * ldq + e % ldq] += v;
+    }
+    for (int r0 = 0; r0 < mk; r0 += kTrRows) {
+        const int rows = min(kTrRows, mk - r0);
+        __syncthreads();  // sz is staged; the previous rows are consumed
+        for (int q = tid; q < rows * k; q += kTrThreads) sG[q] = split_f64(G[(int64_t)r0 * k + q]);
+        __syncthreads();
+        for (int e = tid; e < rows * ldq; e += kTrThreads) {
+            const int rr = e / ldq, c = e % ldq;
+            float sh = 0.f, sl = 0.f;
+            for (int t = 0; t < k; ++t) {
+                const float2 gg = sG[rr * k + t];
+                dd_mac(gg.x, gg.y, sz[t * ldq + c], sh, sl);
+            }
+            out[(int64_t)loc[k + r0 + rr] * ldq + c] += (double)sh + (double)sl;
+        }
+    }
+}
+
+static void matvec_upward_dd(const smash_h2 *h, const float2 *qs2, float2 *qhat2, double *qhat, int ldq,
+                             cudaStream_t s) {
+    const Side &Cs = *h->col;
+    const size_t smem = sizeof(float2) * kTrRows * (size_t)std::max(h->r, 1);
+    allow_max_dynamic_smem((const void *)upward_dd_kernel);
+    for (int l = h->L; l >= 2; --l) {
+        const int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassDDArgs p{n0, h->leaf, Cs.m, Cs.k, Cs.in_off, Cs.sk_off, Cs.loc_off, Cs.g_off, Cs.loc, Cs.G,
+                     qs2, qhat2, qhat, nullptr, ldq};
+        upward_dd_kernel<<<(unsigned)nl, kTrThreads, smem, s>>>(p);
+        LAUNCHED();
+    }
+}
+
+static void matvec_downward_dd(const smash_h2 *h, double *zhat, double *zs, int ldq, cudaStream_t s) {
+    const Side &R = h->row;
+    const size_t kmax = (size_t)std::max(h->r, 1);
+    const size_t smem = sizeof(float2) * (kmax * ldq + kTrRows * kmax);
+    allow_max_dynamic_smem((const void *)downward_dd_kernel);
+    for (int l = 2; l <= h->L; ++l) {
+        const int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        PassDDArgs p{n0, h->leaf, R.m, R.k, R.in_off, R.sk_off, R.loc_off, R.g_off, R.loc, R.G,
+                     nullptr, nullptr, zhat, zs, ldq};
+        downward_dd_kernel<<<(unsigned)nl, kTrThreads, smem, s>>>(p);
+        LAUNCHED();
+    }
+}
+
 void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof, int kid) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
@@ -375,7 +533,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         ksum_dd(h, kid, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();
-    matvec_upward(h, qs, qhat, ldq, s);
+    matvec_upward_dd(h, qs2, qhat2, qhat, ldq, s);
     tm.mark();
     // the coupling: products on the tensor cores (exact digit splits) where
     // the tree allows it, else every operation in double-float on the FP32
@@ -384,7 +542,6 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
     // instructions per entry) is fixed, while the FP32-pipe products cost 12
     // instructions per column.
     auto dd_coupling = [&] {
-        dd_split(qhat, Cs.total_skel * ldq, qhat2, s);
         KsumDDArgs a{};
         a.tnodes = h->nonroot_list; a.t_off = R.sk_off; a.t_cnt = R.k;
         a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
@@ -408,7 +565,7 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
         }
     }
     tm.mark();
-    matvec_downward(h, zhat, zs, ldq, s);
+    matvec_downward_dd(h, zhat, zs, ldq, s);
     tm.mark();
     matvec_scatter(h, zs, ldq, nrhs, Y, s);
     tm.mark();
