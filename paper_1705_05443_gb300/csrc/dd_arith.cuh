@@ -37,6 +37,20 @@ __device__ __forceinline__ void two_sum_ordered(float a, float b, float &s, floa
     e = small - (s - big);
 }
 
+// ------------------------------------------------------------------ differences
+// x - y from three-float coordinates, as a normalised double-float
+__device__ __forceinline__ void diff3(float xh, float xm, float xl, float yh, float ym, float yl, float &dh,
+                                      float &dl) {
+    float a, ea, b, eb;
+    two_sum_ordered(xh, -yh, a, ea);
+    two_sum_ordered(xm, -ym, b, eb);
+    float c = xl - yl;
+    float s, t;
+    two_sum_ordered(a, b, s, t);
+    t = t + ((ea + eb) + c);
+    fast_two_sum(s, t, dh, dl);
+}
+
 // ------------------------------------------------------------------ kernel entries
 // kappa'' = 1/|d| (3D/2D/1D) or 1/d (Cauchy, 1D) in double-float; d = (dh + dl) per axis.
 template <int KID, int D>

@@ -195,6 +195,11 @@ int tc05_take_timeouts();
 // supported for one problem of at most 10 levels, tau < 1, ldq <= 16
 bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq);
 void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s);
+// the near field with the same digit-split products (exact three-float
+// coordinates, FP64 q in, zs out); nodes it cannot take get fallback[i] = 1
+// (i indexes the leaf list) and must be run by the double-float kernel
+bool near_oz_supported(const smash_h2 *h, int kid, int ldq);
+void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, int *fallback, cudaStream_t s);
 void dd_coords(const double *pts, int64_t n, const double *lo, double s, float *out, cudaStream_t st);
 void dd_coords3(const double *pts, int64_t n, int e, float *out, cudaStream_t st);
 int dd_exact_exponent(double s);

@@ -109,20 +109,6 @@ static void dd_split(const double *in, int64_t n, float2 *out, cudaStream_t st) 
     LAUNCHED();
 }
 
-// ------------------------------------------------------------------ differences
-// x - y from three-float coordinates, as a normalised double-float
-__device__ __forceinline__ void diff3(float xh, float xm, float xl, float yh, float ym, float yl, float &dh,
-                                      float &dl) {
-    float a, ea, b, eb;
-    two_sum_ordered(xh, -yh, a, ea);
-    two_sum_ordered(xm, -ym, b, eb);
-    float c = xl - yl;
-    float s, t;
-    two_sum_ordered(a, b, s, t);
-    t = t + ((ea + eb) + c);
-    fast_two_sum(s, t, dh, dl);
-}
-
 // ------------------------------------------------------------------ kernel sums
 struct KsumDDArgs {
     const int32_t *tnodes;
@@ -140,6 +126,7 @@ struct KsumDDArgs {
     int ldq, nchunks, tbp, groups;
     int tile;          // source points staged per round (at least; <= tile_cap)
     int tile_cap;      // shared-memory capacity in sources (the layout's stride)
+    const int *only;   // if set, CTA i runs only when only[i] != 0
 };
 
 constexpr int kDdThreads = 256;
@@ -160,6 +147,7 @@ __global__ void __launch_bounds__(kDdThreads, RC <= 16 ? 3 : 1) ksum_dd_kernel(K
     double *red = reinterpret_cast<double *>(sq + (size_t)cap * a.ldq);  // tbp * ldq
     int64_t *sidx = reinterpret_cast<int64_t *>(red + (size_t)a.tbp * a.ldq);  // cap
 
+    if (a.only && !a.only[blockIdx.x]) return;
     const int64_t g = a.tnodes[blockIdx.x];
     const int T = a.t_cnt[g];
     if (T == 0) return;
@@ -314,9 +302,10 @@ static void ksum_dd_dispatch(int kid, int dim, KsumDDArgs a, int64_t ntn, int RC
 }
 
 // Tuned shape: bit 0 halves the source tile, bit 1 halves the cap of the
-// target block (more source groups per target).
+// target block (more source groups per target).  `untuned` launches the
+// default shape (a launch filtered by `only` would time unrepresentatively).
 static void ksum_dd(const smash_h2 *h, int kid, bool exact, KsumDDArgs a, int64_t ntn, int max_targets, int RC,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool untuned = false) {
     const int dim = h->dim;
     a.nchunks = a.ldq / RC;
     int tbp = 32;
@@ -334,6 +323,10 @@ static void ksum_dd(const smash_h2 *h, int kid, bool exact, KsumDDArgs a, int64_
         else
             ksum_dd_dispatch<false>(kid, dim, b, ntn, RC, s);
     };
+    if (untuned) {
+        run(0);
+        return;
+    }
     char key[160];
     std::snprintf(key, sizeof(key), "ksum_dd/sm%d/k%d/d%d/x%d/rc%d/ld%d/t%lld/n%lld", h->num_sms, kid, dim,
                   exact ? 1 : 0, RC, a.ldq, pow2_at_least(max_targets), pow2_at_least(ntn));
@@ -526,11 +519,32 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
     dd_split(qs, h->ny * ldq, qs2, s);
     tm.mark();
     {
+        // the near field: digit-split products on the tensor cores where the
+        // node allows it (the rest by the double-float kernel), else all in
+        // double-float on the FP32 pipe; the tuner may take either
         KsumDDArgs a{};
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs_x3; a.ys = h->ys_x3; a.qv = qs2; a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq;
-        ksum_dd(h, kid, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
+        const int max_t = (int)std::min<int64_t>(h->leaf_size, 256);
+        if (near_oz_supported(h, kid, ldq)) {
+            int *fallback = tmp.alloc<int>((size_t)std::max<int64_t>(h->nleaves, 1));
+            char key[128];
+            std::snprintf(key, sizeof(key), "near_dd/sm%d/k%d/d%d/ld%d/n%lld", h->num_sms, kid, h->dim, ldq,
+                          pow2_at_least(h->nleaves));
+            tune_choose(key, {0, 1}, ldq >= 8 ? 0 : 1, s, [&](int c) {
+                if (c == 0) {
+                    near_oz(h, kid, qs, zs, ldq, fallback, s);
+                    KsumDDArgs b = a;
+                    b.only = fallback;
+                    ksum_dd(h, kid, true, b, h->nleaves, max_t, RC, s, true);
+                } else {
+                    ksum_dd(h, kid, true, a, h->nleaves, max_t, RC, s);
+                }
+            });
+        } else {
+            ksum_dd(h, kid, true, a, h->nleaves, max_t, RC, s);
+        }
     }
     tm.mark();
     matvec_upward_dd(h, qs2, qhat2, qhat, ldq, s);

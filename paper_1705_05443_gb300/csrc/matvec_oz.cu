@@ -191,22 +191,28 @@ struct KsumOzArgs {
     const int32_t *level;
     const uint64_t *cell;
     double *out;               // target vectors (FP64), ldq
-    double scale;              // 1/s
+    double scale;              // 1/s (coupling), 2^-e (near field, exact frame)
     int ldq, dim;
+    // near field only
+    const float *xt3, *ys3;    // exact three-float coordinates, 12 floats per point
+    int *fallback;             // per CTA: 1 when the node is left to the double-float kernel
+    int same;                  // X = Y: a target meets its own point (entry 0)
 };
 
 // digit bytes per source in shared memory: 6 * NC bf16 plus 16 bytes of pad,
 // which puts the 8 rows of an ldmatrix on distinct banks.  The group
 // reduction at the end of a pass reuses the digit region.
-template <int NC>
+template <int NC, bool NEAR>
 struct OzLayout {
+    static constexpr int kCap = NEAR ? 192 : kOzTileCap;  // sources per tile (three CTAs per SM)
+    static constexpr int kCoordF4 = NEAR ? 3 : 2;          // float4 per source: (hi, lo) or (hi, mid, lo)
     static constexpr int kDigitBytes = kOzDigits * NC * 2;
     static constexpr int kStride = kDigitBytes + 16;
-    static constexpr size_t kCoords = sizeof(float4) * 2 * kOzTileCap;
-    static constexpr size_t kDigits = (size_t)kStride * kOzTileCap;
-    static constexpr size_t kIdx = sizeof(int64_t) * kOzTileCap;
+    static constexpr size_t kCoords = sizeof(float4) * kCoordF4 * kCap;
+    static constexpr size_t kDigits = (size_t)kStride * kCap;
     static constexpr size_t kRed = sizeof(double) * kOzRows * NC;
     static constexpr size_t kAcc = sizeof(float) * 2 * 4 * kOzThreads;  // (hi, lo) of 4 outputs per thread
+    static constexpr size_t kIdx = sizeof(int64_t) * kCap;
     static constexpr size_t kBytes = kCoords + kDigits + kIdx + kAcc;
     static_assert(kRed <= kDigits, "the group reduction fits the digit region");
 };
@@ -284,7 +290,7 @@ __device__ __forceinline__ int oz_row_exponent(float gap2, double node_kb) {
 // are non-negative, so max/min order them), then one Newton step on the
 // hardware reciprocal square root with the residual 1 - r y0^2 formed by FMA
 // and the result renormalised.
-template <int D>
+template <int D, bool ZERO>
 __device__ __forceinline__ void oz_invr(const float *dh, const float *dl, float &kh, float &kl) {
     float p[3], e[3];
 #pragma unroll
@@ -303,6 +309,11 @@ __device__ __forceinline__ void oz_invr(const float *dh, const float *dl, float 
     const float rh = s1 + p[2];
     const float t2 = fminf(s1, p[2]) - (rh - fmaxf(s1, p[2]));
     const float rl = ((e[0] + e[1]) + (e[2] + t1)) + t2;
+    if (ZERO && rh == 0.f) {  // coincident points (near field): the entry is 0
+        kh = 0.f;
+        kl = 0.f;
+        return;
+    }
     const float y0 = rsqrtf(rh);
     const float th = y0 * y0;
     const float tl = fmaf(y0, y0, -th);
@@ -323,8 +334,24 @@ __device__ __forceinline__ void oz_entry(const float4 &xh, const float4 &xl, con
     if (KID == SMASH_K_CAUCHY1D)
         kappa_dd<KID, D>(dh, dl, kh, kl);
     else
-        oz_invr<D>(dh, dl, kh, kl);
+        oz_invr<D, false>(dh, dl, kh, kl);
 }
+
+// the same from exact three-float coordinates (near field: close pairs, and a
+// target's own point, whose entry is 0)
+template <int KID, int D>
+__device__ __forceinline__ void oz_entry3(const float4 *x, const float4 &yh, const float4 &ym, const float4 &yl,
+                                          float &kh, float &kl) {
+    float dh[3], dl[3];
+    diff3(x[0].x, x[1].x, x[2].x, yh.x, ym.x, yl.x, dh[0], dl[0]);
+    diff3(x[0].y, x[1].y, x[2].y, yh.y, ym.y, yl.y, dh[1], dl[1]);
+    diff3(x[0].z, x[1].z, x[2].z, yh.z, ym.z, yl.z, dh[2], dl[2]);
+    if (KID == SMASH_K_CAUCHY1D)
+        kappa_dd<KID, D>(dh, dl, kh, kl);
+    else
+        oz_invr<D, true>(dh, dl, kh, kl);
+}
+
 
 // One CTA per target node.  mma.sync m16n8k16 with the roles
 //   M = 16 right-hand sides (q^ digits, A operand, ldmatrix from the staged tile),
@@ -332,10 +359,12 @@ __device__ __forceinline__ void oz_entry(const float4 &xh, const float4 &xl, con
 //   K = 16 sources,
 // so a warp owns 8 targets, each lane evaluates the 4 entries of its target
 // and 4 sources of a k-block, and the six level sums take 24 registers.
-template <int KID, int D, int NT>
+template <int KID, int D, int NT, bool NEAR>
 __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
     constexpr int NC = 8 * NT;
-    using Lay = OzLayout<NC>;
+    using Lay = OzLayout<NC, NEAR>;
+    constexpr int CAP = Lay::kCap;
+    constexpr int NF = Lay::kCoordF4;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ PartnerChunk pc;
     __shared__ unsigned long long bound_slot;
@@ -343,7 +372,8 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
     __shared__ int plev[kPartnerChunk];
     __shared__ int sfd[kOzLevels * 16];
     __shared__ int rowE[kOzRows];
-    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // [2][cap]: hi, lo
+    __shared__ unsigned int s_dmin[kOzRows], s_dmax[kOzRows];  // near field: squared distances as bits
+    float4 *sy = reinterpret_cast<float4 *>(smraw);                  // [NF][cap]: hi, (mid,) lo
     unsigned char *sd = smraw + Lay::kCoords;                        // [cap][stride]
     int64_t *sidx = reinterpret_cast<int64_t *>(sd + Lay::kDigits);  // [cap]
     // running double-float sums, touched once per tile: [2 * output + (0 hi, 1 lo)][thread]
@@ -358,10 +388,10 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
     const int ldq = a.ldq;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gq = lane >> 2, t4 = lane & 3;
-    for (int i = tid; i < kOzLevels * 16; i += kOzThreads) sfd[i] = a.fd[i];
+    for (int i = tid; i < kOzLevels * 16; i += kOzThreads) sfd[i] = NEAR ? 0 : a.fd[i];
 
-    const double kb_node = oz_node_bound(a, g, e0, e1, &bound_slot);
-    if (!(kb_node < INFINITY)) {
+    const double kb_node = NEAR ? 0.0 : oz_node_bound(a, g, e0, e1, &bound_slot);
+    if (!NEAR && !(kb_node < INFINITY)) {
         // no finite bound: cannot happen for tau < 1 (the build rejects
         // others); write NaN rather than a wrong sum
         for (int q = tid; q < T * ldq; q += kOzThreads) a.out[toff * ldq + q] = NAN;
@@ -378,15 +408,86 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
         const int groups = 8 / wr;        // warps along the sources per target tile
         const int grp = warp / wr, rt = warp % wr;
         const bool active = grp < groups;
-        const int tile = groups == 1 ? 128 : kOzTileCap;  // <= 128 sources per warp per flush
+        const int tile = groups == 1 ? 128 : CAP;  // <= 128 sources per warp per flush
         // the lane's target; targets past the block take target 0's point (finite entries, discarded)
         const int tr = rt * 8 + gq;
-        const float4 *px = reinterpret_cast<const float4 *>(a.xt + (toff + tb + (tr < tcount ? tr : 0)) * 8);
+        const int64_t tpt = toff + tb + (tr < tcount ? tr : 0);
+        const float4 *px = reinterpret_cast<const float4 *>(a.xt + tpt * 8);
         const float4 xh = px[0], xl = px[1];
+        float4 x3[3];
+        if (NEAR) {
+            const float4 *p3 = reinterpret_cast<const float4 *>(a.xt3 + tpt * 12);
+            x3[0] = p3[0];
+            x3[1] = p3[1];
+            x3[2] = p3[2];
+        }
         // first digit: K 2^(8-E); lo(K) enters the fourth digit at 2^24 times that
         float sc0;
         {
-            const int E = oz_row_exponent(oz_point_gap2<D>(xh, a, e0, e1, t4), kb_node);
+            int E;
+            if (NEAR) {
+                // the row's largest entry from its nearest source: hi parts of the
+                // normalised coordinates differ exactly, and the distance is
+                // within sqrt(3) 2^-23 < 2^-22 of theirs; 1/|d| in the exact frame
+                // (x 2^-e, 2^e <= s) is at most 1/|d''|.  Rows whose sources span
+                // more than 2^12 in distance, or meet a coincident point other
+                // than their own, leave the node to the double-float kernel.
+                // every (target, source) pair once: the warps of a target tile
+                // and the lanes of a quad split each staged tile of sources
+                const int64_t self = a.same ? tpt : -1;
+                float dmin2 = INFINITY, dmax2 = 0.f;
+                if (tid < kOzRows) {
+                    s_dmin[tid] = __float_as_uint(INFINITY);
+                    s_dmax[tid] = 0u;
+                }
+                for (int64_t e = e0; e < e1;) {
+                    load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+                    const int total = pc.pre[pc.n];
+                    e += pc.n;
+                    for (int pos = 0; pos < total; pos += CAP) {
+                        const int fill = min(CAP, total - pos);
+                        for (int q = tid; q < fill; q += kOzThreads) {
+                            const int64_t src = chunk_source(pc, pos + q);
+                            sidx[q] = src;
+                            sy[q] = *reinterpret_cast<const float4 *>(a.ys + src * 8);
+                        }
+                        __syncthreads();
+                        if (active)
+                            for (int b = grp * 4 + t4; b < fill; b += 4 * groups) {
+                                if (sidx[b] == self) continue;
+                                const float4 y = sy[b];
+                                const float dx = xh.x - y.x, dy = D > 1 ? xh.y - y.y : 0.f,
+                                            dz = D > 2 ? xh.z - y.z : 0.f;
+                                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                                dmin2 = fminf(dmin2, r2);
+                                dmax2 = fmaxf(dmax2, r2);
+                            }
+                        __syncthreads();
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o));
+                    dmax2 = fmaxf(dmax2, __shfl_xor_sync(0xffffffffu, dmax2, o));
+                }
+                // non-negative floats order as their bit patterns
+                if (active && t4 == 0) {
+                    atomicMin(&s_dmin[tr], __float_as_uint(dmin2));
+                    atomicMax(&s_dmax[tr], __float_as_uint(dmax2));
+                }
+                __syncthreads();
+                dmin2 = __uint_as_float(s_dmin[tr]);
+                dmax2 = __uint_as_float(s_dmax[tr]);
+                const float dlo = sqrtf(dmin2) * (1.0f - 0x1p-20f) - 0x1p-22f;
+                const bool bad = !(dlo > 0.f) || dmax2 > 0x1p24f * dmin2;
+                E = bad ? 0 : ilogbf((1.0f / dlo) * (1.0f + 0x1p-18f)) + 2;
+                if (__syncthreads_or(bad)) {
+                    if (tid == 0) a.fallback[blockIdx.x] = 1;
+                    return;
+                }
+            } else {
+                E = oz_row_exponent(oz_point_gap2<D>(xh, a, e0, e1, t4), kb_node);
+            }
             sc0 = ldexpf(1.0f, 8 - E);
             if (active && grp == 0 && t4 == 0) rowE[tr] = E;
         }
@@ -405,7 +506,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
         for (int64_t e = e0; e < e1;) {
             load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
             const int nchunk = pc.n, total = pc.pre[pc.n];
-            for (int q = tid; q < nchunk; q += kOzThreads) plev[q] = a.level[a.col[e + q]];
+            for (int q = tid; q < nchunk; q += kOzThreads) plev[q] = NEAR ? 0 : a.level[a.col[e + q]];
             __syncthreads();
             if (tid == 0) {
                 int end = nchunk;
@@ -431,10 +532,10 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                 for (int q = tid; q < fill; q += kOzThreads) sidx[q] = chunk_source(pc, pos + q);
                 __syncthreads();
                 // coordinates (the pad up to 16 repeats source 0) and digits (zero pad)
-                for (int q = tid; q < 2 * fill16; q += kOzThreads) {
-                    const int b = q >> 1, hl = q & 1;
+                for (int q = tid; q < NF * fill16; q += kOzThreads) {
+                    const int b = q / NF, part = q - b * NF;
                     const int64_t src = sidx[b < fill ? b : 0];
-                    oz_cp16(sy + hl * kOzTileCap + b, a.ys + src * 8 + 4 * hl);
+                    oz_cp16(sy + part * CAP + b, NEAR ? a.ys3 + src * 12 + 4 * part : a.ys + src * 8 + 4 * part);
                 }
                 constexpr int kPieces = Lay::kDigitBytes / 16;
                 for (int q = tid; q < fill * kPieces; q += kOzThreads) {
@@ -455,8 +556,12 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                         const int cs[4] = {c0, c0 + 1, c0 + 8, c0 + 9};
                         float kh[4], kl[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            oz_entry<KID, D>(xh, xl, sy[cs[u]], sy[kOzTileCap + cs[u]], kh[u], kl[u]);
+                        for (int u = 0; u < 4; ++u) {
+                            if (NEAR)
+                                oz_entry3<KID, D>(x3, sy[cs[u]], sy[CAP + cs[u]], sy[2 * CAP + cs[u]], kh[u], kl[u]);
+                            else
+                                oz_entry<KID, D>(xh, xl, sy[cs[u]], sy[CAP + cs[u]], kh[u], kl[u]);
+                        }
                         // q^ digits of the k-block: A fragments of the six planes
                         uint32_t A[kOzDigits][4];
                         const uint32_t rowaddr = sd_base + (uint32_t)((kbi * 16 + lsrc) * Lay::kStride) + 2u * lrhs;
@@ -546,21 +651,33 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
     }
 }
 
-template <int KID, int D, int NT>
+template <int KID, int D, int NT, bool NEAR>
 static void launch_oz(const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
-    const size_t smem = OzLayout<8 * NT>::kBytes;
-    auto kern = ksum_oz_kernel<KID, D, NT>;
+    const size_t smem = OzLayout<8 * NT, NEAR>::kBytes;
+    auto kern = ksum_oz_kernel<KID, D, NT, NEAR>;
     allow_max_dynamic_smem((const void *)kern);
     kern<<<(unsigned)ntn, kOzThreads, smem, s>>>(a);
     LAUNCHED();
 }
 
-template <int KID, int D>
+template <int KID, int D, bool NEAR>
 static void launch_oz_nt(const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
     if (a.ldq <= 8)
-        launch_oz<KID, D, 1>(a, ntn, s);
+        launch_oz<KID, D, 1, NEAR>(a, ntn, s);
     else
-        launch_oz<KID, D, 2>(a, ntn, s);
+        launch_oz<KID, D, 2, NEAR>(a, ntn, s);
+}
+
+template <bool NEAR>
+static void launch_oz_kernel(const smash_h2 *h, int kid, const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
+    if (kid == SMASH_K_CAUCHY1D)
+        launch_oz_nt<SMASH_K_CAUCHY1D, 1, NEAR>(a, ntn, s);
+    else if (h->dim == 3)
+        launch_oz_nt<SMASH_K_INVR, 3, NEAR>(a, ntn, s);
+    else if (h->dim == 2)
+        launch_oz_nt<SMASH_K_INVR, 2, NEAR>(a, ntn, s);
+    else
+        launch_oz_nt<SMASH_K_INVR, 1, NEAR>(a, ntn, s);
 }
 
 bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq) {
@@ -592,15 +709,87 @@ void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, i
     a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
     a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.dig = dig; a.fd = fd; a.colscale = colscale;
     a.level = h->level; a.cell = h->cell; a.out = zhat; a.scale = 1.0 / h->s; a.ldq = ldq; a.dim = h->dim;
-    const int64_t ntn = h->nnodes - h->nroots;
-    if (kid == SMASH_K_CAUCHY1D)
-        launch_oz_nt<SMASH_K_CAUCHY1D, 1>(a, ntn, s);
-    else if (h->dim == 3)
-        launch_oz_nt<SMASH_K_INVR, 3>(a, ntn, s);
-    else if (h->dim == 2)
-        launch_oz_nt<SMASH_K_INVR, 2>(a, ntn, s);
-    else
-        launch_oz_nt<SMASH_K_INVR, 1>(a, ntn, s);
+    launch_oz_kernel<false>(h, kid, a, h->nnodes - h->nroots, s);
+    tmp.release();
+}
+
+// ------------------------------------------------------------------ near field
+// The near field (3.20) with the same digit-split products: sources are the
+// points of the neighbouring leaves, q the sorted input vectors (one exponent
+// per column), entries from the exact three-float coordinates.  A row's
+// exponent comes from its nearest source; nodes with coincident points or a
+// spread of distances above 2^12 are flagged in `fallback` and left to the
+// double-float kernel.
+
+// max |q_pc| per column over all points (non-negative doubles order as their bits)
+__global__ void oz_colmax_flat_kernel(const double *__restrict__ q, int64_t n, int ldq,
+                                      unsigned long long *__restrict__ cmax) {
+    __shared__ unsigned long long sm[16];
+    if (threadIdx.x < 16) sm[threadIdx.x] = 0ull;
+    __syncthreads();
+    // the grid stride is a multiple of ldq (a power of two <= 16): one column per thread
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(i % ldq);
+    unsigned long long m = 0ull;
+    for (; i < n * ldq; i += stride) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(q[i]));
+        m = b > m ? b : m;
+    }
+    if (m) atomicMax(&sm[c], m);
+    __syncthreads();
+    if (threadIdx.x < ldq && sm[threadIdx.x]) atomicMax(&cmax[threadIdx.x], sm[threadIdx.x]);
+}
+
+// dig[(p * 6 + t) * NC + c] = b_t of q_pc 2^-fref_c (zero for c >= ldq)
+__global__ void oz_digits_flat_kernel(const double *__restrict__ q, int64_t n, int ldq, int NC,
+                                      const int *__restrict__ fref, __nv_bfloat16 *__restrict__ dig) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * NC) return;
+    const int64_t p = i / NC;
+    const int c = (int)(i % NC);
+    double x = c < ldq ? ldexp(q[p * ldq + c], -fref[c]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kOzDigits; ++u) {
+        x *= 256.0;
+        const double d = rint(x);
+        x -= d;
+        dig[(p * kOzDigits + u) * NC + c] = __float2bfloat16_rn((float)d);
+    }
+}
+
+bool near_oz_supported(const smash_h2 *h, int kid, int ldq) {
+    return ldq <= 16 && (kid == SMASH_K_INVR || kid == SMASH_K_CAUCHY1D) && h->nleaves > 0 && h->xs_dd && h->ys_dd &&
+           h->xs_x3 && h->ys_x3;
+}
+
+void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, int *fallback, cudaStream_t s) {
+    const int NC = ldq <= 8 ? 8 : 16;
+    Arena tmp(s);
+    unsigned long long *cmax = tmp.alloc<unsigned long long>(kOzLevels * 16);
+    int *fd = tmp.alloc<int>(kOzLevels * 16);
+    int *fref = tmp.alloc<int>(16);
+    double *colscale = tmp.alloc<double>(16);
+    __nv_bfloat16 *dig = tmp.alloc<__nv_bfloat16>((size_t)std::max<int64_t>(h->ny, 1) * kOzDigits * NC);
+    CK(cudaMemsetAsync(cmax, 0, kOzLevels * 16 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(fallback, 0, sizeof(int) * (size_t)h->nleaves, s));
+    const int64_t work = h->ny * ldq;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4 * (int64_t)h->num_sms));
+    oz_colmax_flat_kernel<<<blocks, 256, 0, s>>>(qs, h->ny, ldq, cmax);
+    LAUNCHED();
+    oz_scales_kernel<<<1, 32, 0, s>>>(cmax, fd, fref, colscale);
+    LAUNCHED();
+    const int64_t nd = h->ny * NC;
+    oz_digits_flat_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(qs, h->ny, ldq, NC, fref, dig);
+    LAUNCHED();
+    KsumOzArgs a{};
+    a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
+    a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
+    a.xt = h->xs_dd; a.ys = h->ys_dd; a.xt3 = h->xs_x3; a.ys3 = h->ys_x3;
+    a.dig = dig; a.fd = fd; a.colscale = colscale; a.level = h->level; a.cell = h->cell;
+    a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq; a.dim = h->dim;
+    a.fallback = fallback; a.same = h->same;
+    launch_oz_kernel<true>(h, kid, a, h->nleaves, s);
     tmp.release();
 }
 

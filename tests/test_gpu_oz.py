@@ -146,3 +146,62 @@ def test_wide_blocks_take_the_double_float_coupling(clean_table, tmp_path, nrhs)
     assert not keys
     assert _rel(h.matvec(_dev(q), precision=F32X2).cpu().numpy(), zo) <= RTOL
     h.close()
+
+
+# ------------------------------------------------------------------ near field
+def _near_keys(h, q, tmp_path):
+    sm.smash_set_autotune(True)
+    h.matvec(_dev(q), precision=F32X2)
+    sm.smash_set_autotune(False)
+    path = tmp_path / "n.json"
+    sm.smash_autotune_save(str(path))
+    table = json.loads(path.read_text())["entries"]
+    return table, [k for k in table if k.startswith("near_dd/")], path
+
+
+@pytest.mark.parametrize("case", ["cube3", "sphere", "plane2", "line1", "cauchy"])
+def test_both_near_fields_match_the_oracle(clean_table, tmp_path, case):
+    """The near field (3.20) by digit-split products on the tensor cores
+    (rows scaled by their nearest source, nodes with coincident points or a
+    wide spread of distances left to the double-float kernel) and all in
+    double-float: both meet the bar and agree far below it."""
+    y = None
+    if case == "cube3":
+        x, kern, leaf, order, tol = si.uniform_cube(12000, 3, 6600), sm.SMASH_K_INVR, 64, 4, 1e-8
+    elif case == "sphere":
+        x, kern, leaf, order, tol = si.sphere_with_caps(12000, 6601), sm.SMASH_K_INVR, 64, 4, 1e-8
+    elif case == "plane2":
+        x, kern, leaf, order, tol = si.uniform_cube(8000, 2, 6602), sm.SMASH_K_INVR, 64, 5, 1e-8
+    elif case == "line1":
+        x, kern, leaf, order, tol = si.uniform_cube(5000, 1, 6603), sm.SMASH_K_INVR, 64, 8, 1e-8
+    else:
+        (x, y), kern, leaf, order, tol = si.cauchy_1d(6000, 6604), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10
+    n = len(x) if y is None else len(y)
+    q = si.rhs(n, 16, 6605)
+    zo = oracle.H2(x, kern, leaf, order, tol, y=y).matvec(q)
+    h = sm.H2Matrix(_dev(x), kern, leaf, order, tol, y=None if y is None else _dev(y))
+    table, keys, path = _near_keys(h, q, tmp_path)
+    assert keys, "the digit-split near field is offered"
+    z0 = _forced(h, q, table, keys, path, 0)
+    z1 = _forced(h, q, table, keys, path, 1)
+    assert _rel(z0, zo) <= RTOL
+    assert _rel(z1, zo) <= RTOL
+    assert _rel(z0, z1) <= 1e-12
+    h.close()
+
+
+def test_coincident_points_take_the_double_float_near_field(clean_table, tmp_path):
+    """Duplicated points (distinct indices, equal coordinates) have entry 0 and
+    no positive nearest distance: their leaves fall back to the double-float
+    kernel inside the digit-split path, and the result meets the bar."""
+    x = si.uniform_cube(8000, 3, 6700)
+    x = np.concatenate([x, x[:300]])  # 300 coincident pairs
+    q = si.rhs(len(x), 16, 6701)
+    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
+    table, keys, path = _near_keys(h, q, tmp_path)
+    assert keys
+    z0 = _forced(h, q, table, keys, path, 0)
+    assert np.all(np.isfinite(z0))
+    assert _rel(z0, zo) <= RTOL
+    h.close()
