@@ -94,7 +94,8 @@ def load_library(build: bool = True):
     if build:
         _build.build()
     if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"the SMASH CUDA library is missing ({_build.LIB}); run __graft_entry__.build()")
+        raise RuntimeError(f"the SMASH CUDA library is missing ({_build.LIB}); build it with "
+                           "paper_1705_05443_gb300._build.build()")
     lib = C.CDLL(_build.LIB)
     P, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
     lib.smash_default_options.argtypes = [P]

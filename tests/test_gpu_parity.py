@@ -1,6 +1,6 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
 
-Bars (stated here, derived in the design doc):
+Bars, each with the reason it holds:
   - partition, Morton keys, permutations, tree arrays, L and L^- lists:
     bit-exact (integer work);
   - ranks, skeleton and rest index sets: bit-exact;
