@@ -29,9 +29,11 @@
 //    2^24, and every digit (<= 256) is exact in bf16: the FP32 accumulation
 //    of bf16 x bf16 products
 //    (mma.sync m16n8k16) is exact for every level.  After each tile (at most
-//    128 sources per warp) the six level sums are combined by error-free
-//    transformations, scaled by 2^(F_lc - max_l F_lc) (exact), into a
-//    double-float accumulator per output.
+//    128 sources per warp) the six level sums are folded into a double-float
+//    accumulator per output: levels 0-2 by exact TwoSums, levels 3-5 as a
+//    float32 tail at weight 2^-24, off by at most 2^-22 level-0 units (2^-46
+//    of a full-scale level sum); the level's scale 2^(F_lc - max_l F_lc) is
+//    exact.
 //
 // The result keeps the double-float coupling's precision (~2^-46 per entry)
 // while the FP32 pipe evaluates only the entries and their digits; the
