@@ -618,7 +618,7 @@ def bench_ours(args, w):
                                                      3: "1/(x-y)"}[w["kernel"]],
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
                    "precision": "build fp64; matvec " + {sm.SMASH_PREC_F64: "fp64",
-                                                          sm.SMASH_PREC_F32X2: "double-float kernel sums, fp64 transfers",
+                                                          sm.SMASH_PREC_F32X2: "double-float kernel sums and transfers; coupling and near-field products as exact 8-bit digit products on the tensor cores",
                                                           sm.SMASH_PREC_F32: "fp32 kernel sums, fp64 transfers",
                                                           sm.SMASH_PREC_TF32: "tf32 coupling products, fp32 near field",
                                                           sm.SMASH_PREC_BF16: "bf16 coupling products, fp32 near field",
