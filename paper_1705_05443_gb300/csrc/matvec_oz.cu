@@ -434,8 +434,9 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                 // (x 2^-e, 2^e <= s) is at most 1/|d''|.  Rows whose sources span
                 // more than 2^12 in distance, or meet a coincident point other
                 // than their own, leave the node to the double-float kernel.
-                // every (target, source) pair once: the warps of a target tile
-                // and the lanes of a quad split each staged tile of sources
+                //
+                // Every (target, source) pair is visited once: the warps of a
+                // target tile and the lanes of a quad split each staged tile.
                 const int64_t self = a.same ? tpt : -1;
                 float dmin2 = INFINITY, dmax2 = 0.f;
                 if (tid < kOzRows) {
