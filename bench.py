@@ -53,7 +53,7 @@ OZ_EVAL_OPS = 43 + 23
 OZ_PRODUCTS = 21
 # DRAM bytes of one digit-split coupling launch (3D 1/r, N = 2^18, 16 RHS,
 # 6.099e9 entries) from ncu (profiles/ksum_oz_coupling_3d_invr_262144.md)
-OZ_COUPLING_TRAFFIC = (73.347328e6 + 21.123072e6, 6099084090)
+OZ_COUPLING_TRAFFIC = (73.693184e6 + 20.957184e6, 6099084090)
 
 
 def _coupling_choice(sm, nrhs):
