@@ -10,6 +10,11 @@ integer coordinates c place it at lo + c 2^(1-l) s.  This test checks, on
 trees the oracle builds (the library's trees are identical, see the parity
 tests), that every point of a node lies in its cell and that every entry of
 every admissible pair obeys both bounds.
+
+The near field's digit split has no geometric bound (its pairs are not
+admissible); it scales a row by its nearest source, found from the float32
+hi parts of the normalised coordinates with a margin.  The last tests check
+that this distance is a lower bound of every distance of the row.
 """
 import numpy as np
 import pytest
@@ -81,3 +86,47 @@ def test_entry_bounds_hold_on_clustered_sphere():
 def test_entry_bounds_hold_for_rectangular_cauchy():
     x, y = si.cauchy_1d(2000, 8104)
     _check(x, y, 3, 32, 8, 1e-8)
+
+
+def _near_check(x, d, leaf, seed_kernel=1):
+    """The near field's row bound: from the hi parts of the normalised
+    coordinates x'' = 1 + (x - lo)/s (float32), the kernel takes
+    dlo = sqrt(min hi-part r^2) (1 - 2^-20) - 2^-22 as a lower bound of every
+    distance |x'' - y''| of the row (the target's own point skipped)."""
+    h = oracle.H2(x, seed_kernel, leaf, 3, 1e-6)
+    e = h.export()
+    lo, s = np.asarray(e["lo"])[:d], float(e["s"])
+    xs = x[np.asarray(e["permx"])]
+    xn = 1.0 + (xs - lo) / s                         # FP64 normalised coordinates
+    xh = xn.astype(np.float32)                       # their hi parts
+    rs, rc, cs, cc = (np.asarray(e[k]) for k in ("rs", "rc", "cs", "cc"))
+    ptr, col = np.asarray(e["near_ptr"]), np.asarray(e["near_col"])
+    leaves = np.flatnonzero(np.asarray(e["leaf"]))
+    checked = 0
+    for g in leaves:
+        if rc[g] == 0 or ptr[g] == ptr[g + 1]:
+            continue
+        tgt = np.arange(rs[g], rs[g] + rc[g])
+        src = np.concatenate([np.arange(cs[j], cs[j] + cc[j]) for j in col[ptr[g]:ptr[g + 1]]])
+        dh = xh[tgt][:, None, :].astype(np.float32) - xh[src][None, :, :]   # exact (Sterbenz)
+        r2 = np.zeros(dh.shape[:2], dtype=np.float32)
+        for a in range(d):                                                 # the kernel's fma chain
+            r2 = (dh[:, :, a].astype(np.float64) ** 2 + r2.astype(np.float64)).astype(np.float32)
+        true = np.sqrt(((xn[tgt][:, None, :] - xn[src][None, :, :]) ** 2).sum(2))
+        self_pair = tgt[:, None] == src[None, :]
+        r2 = np.where(self_pair, np.inf, r2)
+        dlo = np.sqrt(r2.min(1).astype(np.float64)).astype(np.float32) * np.float32(1 - 2.0 ** -20) \
+            - np.float32(2.0 ** -22)
+        mtrue = np.where(self_pair, np.inf, true).min(1)
+        assert np.all(dlo <= mtrue), g
+        checked += 1
+    assert checked > 0
+
+
+@pytest.mark.parametrize("d,n,leaf,seed", [(3, 3000, 32, 8200), (2, 2500, 32, 8201), (1, 1500, 16, 8202)])
+def test_near_field_row_bound_is_a_lower_bound(d, n, leaf, seed):
+    _near_check(si.uniform_cube(n, d, seed), d, leaf)
+
+
+def test_near_field_row_bound_on_clustered_sphere():
+    _near_check(si.sphere_with_caps(2500, 8203), 3, 32)
