@@ -70,10 +70,13 @@ enum {
 /* Arithmetic of the matvec (Section 3.4).  The build is always FP64. */
 enum {
     SMASH_PREC_F64 = 0,   /* FP64 kernel evaluation, transfers and sums */
-    SMASH_PREC_F32X2 = 1, /* coupling and near field in double-float arithmetic on the FP32
-                             pipe (each value hi + lo floats, error-free products and sums,
-                             ~1e-12 relative to FP64); transfers FP64.  Kernels 1/|x-y| and
-                             1/(x-y) only. */
+    SMASH_PREC_F32X2 = 1, /* coupling, near field and transfers in double-float arithmetic
+                             on the FP32 pipe (each value hi + lo floats, error-free products
+                             and sums).  From 8 right-hand sides per pass the coupling and
+                             near-field products run on the tensor cores instead, as exact
+                             products of 8-bit digits of the double-float entries and
+                             vectors (Section 3.4, (3.19)-(3.20)).  ~1e-12 relative to FP64
+                             either way.  Kernels 1/|x-y| and 1/(x-y) only. */
     SMASH_PREC_F32 = 2,   /* mixed precision: coupling and near field in FP32 (kernel entries,
                              products, sums; the near field with Kahan-compensated sums),
                              differences from two-float coordinates; transfers FP64.
