@@ -16,6 +16,10 @@ Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
   H^2 matvec ............... pinned (dense on small/trivial trees, symmetry,
                              telescoping form (3.21)-(3.26) on perfect trees,
                              error falling with the order)
+  |H^2| row scales ......... pinned (dense sum |kappa||q| when nothing is
+                             admissible; triangle inequality against the
+                             matvec; not below the dense sum |kappa||q| by
+                             more than the approximation error)
   parameter heuristic ...... pinned (the three worked values of Section 6.1)
 """
 from __future__ import annotations
@@ -72,6 +76,8 @@ def _load():
         lib.orc_matvec.argtypes = [P, P, P, i32]
         lib.orc_matvec_leaves.argtypes = [P, P, P, i32, P, i64]
         lib.orc_matvec_leaves.restype = i32
+        lib.orc_matvec_abs.argtypes = [P, P, P, i32, P, i64]
+        lib.orc_matvec_abs.restype = i32
         lib.orc_dense_rows.argtypes = [P, i64, P, i64, i32, i32, P, i32, P, i64, P]
         lib.orc_dense_rows.restype = None
         lib.orc_query.restype = i64
@@ -273,6 +279,26 @@ class H2:
         st = _load().orc_matvec_leaves(self._h, _ptr(q), _ptr(z), q.shape[1], _ptr(leaves), len(leaves))
         if st != 0:
             raise ValueError("matvec_leaves: not a leaf gid")
+        return z
+
+    def matvec_abs(self, q, leaves=None) -> np.ndarray:
+        """Row scales of A^ q: the matvec with every factor (q, G, kappa)
+        replaced by its magnitude, so each entry is the sum of |terms| that
+        matvec() adds up for it -- the scale of its rounding error.  With
+        leaves, only the rows of those leaf gids are computed (others NaN)."""
+        q = np.ascontiguousarray(_f64(q))
+        if q.ndim == 1:
+            q = q[:, None]
+        nx = self.query("nx")
+        if leaves is None:
+            z = np.empty((nx, q.shape[1]))
+            _load().orc_matvec_abs(self._h, _ptr(q), _ptr(z), q.shape[1], None, 0)
+            return z
+        leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+        z = np.full((nx, q.shape[1]), np.nan)
+        st = _load().orc_matvec_abs(self._h, _ptr(q), _ptr(z), q.shape[1], _ptr(leaves), len(leaves))
+        if st != 0:
+            raise ValueError("matvec_abs: not a leaf gid")
         return z
 
     def export(self) -> dict:

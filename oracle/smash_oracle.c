@@ -764,15 +764,23 @@ void orc_free(orc_h2 *h)
 
 /* need == NULL: every node.  Otherwise only the nodes flagged in need get
  * their coupling, downward and near-field work, and only the rows of the
- * flagged leaves of z are written (the upward pass is always complete). */
-static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nrhs, const unsigned char *need)
+ * flagged leaves of z are written (the upward pass is always complete).
+ * absval != 0: the same passes with every factor replaced by its magnitude
+ * (|q|, |G|, |kappa|), so that each output is the sum of the magnitudes of
+ * the terms the plain matvec adds up for it, step by step.  A sum of terms
+ * t_1..t_n computed in floating point differs from the exact sum by at most
+ * a small multiple of the unit roundoff times sum |t_i|; this is that scale
+ * for every row of A^ q. */
+#define ORC_ABS(v) (absval ? fabs(v) : (v))
+static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nrhs, const unsigned char *need,
+                             int absval)
 {
     int d = h->d;
     int64_t nx = h->nx, ny = h->ny;
     double *qs = malloc(sizeof(double) * (size_t)ny * nrhs);
     double *zs = calloc((size_t)nx * nrhs, sizeof(double));
     for (int64_t pnt = 0; pnt < ny; ++pnt)
-        for (int c = 0; c < nrhs; ++c) qs[pnt * nrhs + c] = q[h->permy[pnt] * nrhs + c];
+        for (int c = 0; c < nrhs; ++c) qs[pnt * nrhs + c] = ORC_ABS(q[h->permy[pnt] * nrhs + c]);
     double **qhat = calloc((size_t)h->nnodes, sizeof(double *));
     double **zhat = calloc((size_t)h->nnodes, sizeof(double *));
     /* step 1: upward pass, q^_i = V_i^T q|_i at leaves, sum_c W_c^T q^_c above */
@@ -797,7 +805,7 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
                 for (int c = 0; c < nrhs; ++c) {
                     double s = in[(size_t)cp->skel_loc[t] * nrhs + c];
                     for (int u = 0; u < m - k; ++u)
-                        s = s + cp->G[(size_t)u * k + t] * in[(size_t)cp->rest_loc[u] * nrhs + c];
+                        s = s + ORC_ABS(cp->G[(size_t)u * k + t]) * in[(size_t)cp->rest_loc[u] * nrhs + c];
                     qhat[g][(size_t)t * nrhs + c] = s;
                 }
             free(in);
@@ -813,7 +821,7 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
             for (int a = 0; a < ci->k; ++a) {
                 const double *xa = h->xs + ci->skel[a] * d;
                 for (int bb = 0; bb < cj->k; ++bb) {
-                    double kv = orc_kernel(h->kid, d, xa, h->ys + cj->skel[bb] * d);
+                    double kv = ORC_ABS(orc_kernel(h->kid, d, xa, h->ys + cj->skel[bb] * d));
                     for (int c = 0; c < nrhs; ++c)
                         zhat[g][(size_t)a * nrhs + c] += kv * qhat[j][(size_t)bb * nrhs + c];
                 }
@@ -835,7 +843,7 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
                 for (int c = 0; c < nrhs; ++c) {
                     double s = 0.0;
                     for (int t = 0; t < k; ++t)
-                        s = s + cp->G[(size_t)u * k + t] * zhat[g][(size_t)t * nrhs + c];
+                        s = s + ORC_ABS(cp->G[(size_t)u * k + t]) * zhat[g][(size_t)t * nrhs + c];
                     out[(size_t)cp->rest_loc[u] * nrhs + c] = s;
                 }
             if (nd->leaf) {
@@ -859,7 +867,7 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
             const orc_node *nj = &h->nodes[h->near_col[e]];
             for (int64_t a = ni->rs; a < ni->rs + ni->rc; ++a)
                 for (int64_t bb = nj->cs; bb < nj->cs + nj->cc; ++bb) {
-                    double kv = orc_kernel(h->kid, d, h->xs + a * d, h->ys + bb * d);
+                    double kv = ORC_ABS(orc_kernel(h->kid, d, h->xs + a * d, h->ys + bb * d));
                     for (int c = 0; c < nrhs; ++c) zs[a * nrhs + c] += kv * qs[bb * nrhs + c];
                 }
         }
@@ -879,9 +887,11 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
     return 0;
 }
 
+#undef ORC_ABS
+
 int orc_matvec(const orc_h2 *h, const double *q, double *z, int nrhs)
 {
-    return orc_matvec_masked(h, q, z, nrhs, NULL);
+    return orc_matvec_masked(h, q, z, nrhs, NULL, 0);
 }
 
 /* Rows of A^ q for the points of the given leaves only (gids), computed
@@ -897,7 +907,25 @@ int orc_matvec_leaves(const orc_h2 *h, const double *q, double *z, int nrhs, con
         if (g < 0 || g >= h->nnodes || !h->nodes[g].leaf) { free(need); return -1; }
         while (g >= 0) { need[g] = 1; g = h->nodes[g].parent; }
     }
-    int st = orc_matvec_masked(h, q, z, nrhs, need);
+    int st = orc_matvec_masked(h, q, z, nrhs, need, 0);
+    free(need);
+    return st;
+}
+
+/* Row scales of A^ q: the matvec above with every factor replaced by its
+ * magnitude (see orc_matvec_masked).  leaves == NULL: every row; otherwise
+ * only the rows of the given leaves are written. */
+int orc_matvec_abs(const orc_h2 *h, const double *q, double *z, int nrhs, const int32_t *leaves,
+                   int64_t nleaves)
+{
+    if (!leaves) return orc_matvec_masked(h, q, z, nrhs, NULL, 1);
+    unsigned char *need = calloc((size_t)h->nnodes, 1);
+    for (int64_t t = 0; t < nleaves; ++t) {
+        int g = leaves[t];
+        if (g < 0 || g >= h->nnodes || !h->nodes[g].leaf) { free(need); return -1; }
+        while (g >= 0) { need[g] = 1; g = h->nodes[g].parent; }
+    }
+    int st = orc_matvec_masked(h, q, z, nrhs, need, 1);
     free(need);
     return st;
 }

@@ -485,12 +485,20 @@ def test_h2_id_structure_at_every_node():
         assert np.linalg.norm(U) <= 2.0 * np.sqrt(len(ibar[g]) * max(1, len(skel[g])))
 
 
-def _telescoping_matvec(e, x, kid, q):
+def _telescoping_matvec(e, x, kid, q, absval=False):
     """(3.24)-(3.26) on a perfect tree, written with dense block-diagonal
-    U^(l) (3.22) and dense coupling blocks B^(l) from the skeleton indices."""
+    U^(l) (3.22) and dense coupling blocks B^(l) from the skeleton indices.
+    absval: the same products with every generator, kernel entry and q
+    replaced by its magnitude."""
     L = e["L"]
     xs = x[e["permx"]]
     ibar, skel, rest, G = local_positions(e, "row")
+    if absval:
+        G = [np.abs(g) for g in G]
+        q = np.abs(q)
+        kmat = lambda k, a, b: np.abs(kernel_matrix(k, a, b))
+    else:
+        kmat = kernel_matrix
     lvl = lambda l: range(e["lvl_off"][l - 1], e["lvl_off"][l])
     Ublk = {}
     for l in range(2, L + 1):
@@ -519,7 +527,7 @@ def _telescoping_matvec(e, x, kid, q):
                 j = int(e["adm_col"][t])
                 assert e["level"][j] == l
                 B[offs[i]:offs[i] + len(skel[i]), offs[j]:offs[j] + len(skel[j])] = \
-                    kernel_matrix(kid, xs[skel[i]], xs[skel[j]])
+                    kmat(kid, xs[skel[i]], xs[skel[j]])
         zhat[l] = B @ qhat[l]
     # B^(L): near field
     n = len(xs)
@@ -528,7 +536,7 @@ def _telescoping_matvec(e, x, kid, q):
         for t in range(e["near_ptr"][i], e["near_ptr"][i + 1]):
             j = int(e["near_col"][t])
             BL[e["rs"][i]:e["rs"][i] + e["rc"][i], e["cs"][j]:e["cs"][j] + e["cc"][j]] = \
-                kernel_matrix(kid, xs[e["rs"][i]:e["rs"][i] + e["rc"][i]], xs[e["cs"][j]:e["cs"][j] + e["cc"][j]])
+                kmat(kid, xs[e["rs"][i]:e["rs"][i] + e["rc"][i]], xs[e["cs"][j]:e["cs"][j] + e["cc"][j]])
     # (3.26)
     w = Ublk[2] @ zhat[2]
     for l in range(3, L + 1):
@@ -552,6 +560,52 @@ def test_h2_nodewise_matvec_equals_telescoping_form(d, cells, per_cell, p, kid):
     assert rel(z, z_tel) < 1e-12
     # and the approximation is a real one
     assert 0 < rel(z, kernel_matrix(kid, x, x) @ q) < 1e-2
+
+
+# ---------------------------------------------------------------- row scales of A^ q
+def test_h2_abs_matvec_is_dense_abs_when_root_is_a_leaf():
+    x = si.uniform_cube(120, 2, 121)
+    q = si.rhs(120, 3, 122)
+    h = oracle.H2(x, 0, 128, 4, 1e-8)
+    assert h.query("nadm") == 0
+    assert rel(h.matvec_abs(q), np.abs(kernel_matrix(0, x, x)) @ np.abs(q)) < 1e-14
+
+
+@pytest.mark.parametrize("d,cells,per_cell,p,kid", [(2, 16, 16, 3, 0), (1, 64, 8, 5, 3), (3, 4, 16, 2, 1)])
+def test_h2_abs_matvec_equals_telescoping_form_of_magnitudes(d, cells, per_cell, p, kid):
+    """On perfect trees the node-wise sums of |terms| equal (3.24)-(3.26)
+    written with |U^(l)|, |B^(l)| and |q|: both expand to the same sum over
+    paths of products of nonnegative factors."""
+    x = si.jittered_grid(cells, d, 90 + d, per_cell=per_cell)
+    q = si.rhs(len(x), 2, 91)
+    h = oracle.H2(x, kid, per_cell, p, 1e-10)
+    e = h.export()
+    za = h.matvec_abs(q)
+    assert rel(za, _telescoping_matvec(e, x, kid, q, absval=True)) < 1e-12
+    assert rel(za, _telescoping_matvec(e, x, kid, q)) > 1e-2   # not the signed sums
+
+
+@pytest.mark.parametrize("kid,d,n", [(0, 2, 3000), (1, 3, 4000), (2, 3, 3000)])
+def test_h2_abs_matvec_bounds(kid, d, n):
+    """Triangle inequality: |(A^ q)_i| <= (|A^| |q|)_i, row by row.  And
+    (|A^| |q|)_i >= sum_j |A_ij| |q_j| - sum_j |E_ij| |q_j| with E = A^ - A,
+    so it is not below the dense sum of magnitudes by more than the
+    approximation error (here ~1e-3 per entry at order 4)."""
+    x = si.gaussian_mixture(n, d, 3, sigma=0.1) if kid == 2 else si.uniform_cube(n, d, 130 + kid)
+    q = si.rhs(n, 3, 131)
+    h = oracle.H2(x, kid, 32, 4, 1e-8)
+    assert h.query("nadm") > 0
+    za, z = h.matvec_abs(q), h.matvec(q)
+    assert np.all(za >= np.abs(z) * (1 - 1e-13))
+    rows = si.sample_rows(n, 200, 132)
+    dense_abs = np.abs(kernel_matrix(kid, x[rows], x)) @ np.abs(q)
+    assert np.all(za[rows] >= 0.99 * dense_abs)
+    # a sampled leaf set gives the same rows
+    e = h.export()
+    leaves = np.flatnonzero(e["leaf"])[[0, 3, -1]].astype(np.int32)
+    zs = h.matvec_abs(q, leaves)
+    sel = np.concatenate([e["permx"][e["rs"][g]:e["rs"][g] + e["rc"][g]] for g in leaves])
+    assert np.array_equal(zs[sel], za[sel])
 
 
 def test_h2_rectangular_cauchy_close_to_dense():
