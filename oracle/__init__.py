@@ -21,6 +21,13 @@ Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
                              matvec; not below the dense sum |kappa||q| by
                              more than the approximation error)
   parameter heuristic ...... pinned (the three worked values of Section 6.1)
+  Taylor basis on C ........ pinned ((2.4) with the coefficients (2.5) within
+                             the bound (2.6); eta, powers and factorials)
+  complex compr ............ pinned (LAPACK's complex QRCP, rank, |A| <= f,
+                             volume growth of each swap)
+  complex H^2 matvec ....... pinned (dense when the root is a leaf,
+                             antisymmetry of 1/(x-y), error falling with r,
+                             the error magnitudes of Table 6.1)
 """
 from __future__ import annotations
 
@@ -35,6 +42,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "smash_oracle.c")
 _OUT = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT, "liboracle.so")
+# ORACLE_OPENMP=1 loads the same source built with -fopenmp (threads from
+# OMP_NUM_THREADS): identical results, node and row loops on several cores;
+# used only to report a multi-core CPU baseline beside the serial one
+_OMP_PATH = os.path.join(_OUT, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -46,18 +57,28 @@ _Q = dict(nx=0, ny=1, L=2, nnodes=3, nadm=4, nnear=5, same=6, skel_row=7, rest_r
           badswap=16)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction) into oracle/_build."""
-    os.makedirs(_OUT, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+def _compile(path: str, extra, force: bool) -> str:
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *extra,
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) into oracle/_build:
+    the serial library and its -fopenmp twin."""
+    os.makedirs(_OUT, exist_ok=True)
+    _compile(_OMP_PATH, ["-fopenmp"], force)
+    return _compile(_LIB_PATH, [], force)
+
+
+def openmp() -> bool:
+    """True when this process loads the -fopenmp build (ORACLE_OPENMP=1)."""
+    return os.environ.get("ORACLE_OPENMP", "0") == "1"
 
 
 def _load():
@@ -66,7 +87,7 @@ def _load():
         if _lib is not None:
             return _lib
         build()
-        lib = C.CDLL(_LIB_PATH)
+        lib = C.CDLL(_OMP_PATH if openmp() else _LIB_PATH)
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int, C.c_double
         lib.orc_build.restype = P
@@ -112,6 +133,22 @@ def _load():
         lib.orc_export_lists.restype = None
         lib.orc_export_comp.argtypes = [P, i32, P, P, P, P, P]
         lib.orc_export_comp.restype = None
+        lib.orc_taylor_coefficients.argtypes = [i32, P]
+        lib.orc_taylor_coefficients.restype = None
+        lib.orc_taylor_basis_t.argtypes = [i32, P, dbl, dbl, dbl, P, i32, P]
+        lib.orc_taylor_basis_t.restype = None
+        lib.orc_compr_c.argtypes = [P, i32, i32, dbl, dbl, P, P, P, P]
+        lib.orc_compr_c.restype = i32
+        lib.orc_build_taylor.restype = P
+        lib.orc_build_taylor.argtypes = [P, i64, i32, i32, dbl, dbl, dbl, dbl, dbl]
+        lib.orc_matvec_taylor.argtypes = [P, P, P, i32, i32]
+        lib.orc_matvec_taylor.restype = i32
+        lib.orc_dense_rows_taylor.argtypes = [P, i64, P, i32, P, i64, dbl, dbl, P]
+        lib.orc_dense_rows_taylor.restype = None
+        lib.orc_export_taylor.argtypes = [P] * 6
+        lib.orc_export_taylor.restype = None
+        lib.orc_cauchy_c_entry.argtypes = [P, P, dbl, dbl, P]
+        lib.orc_cauchy_c_entry.restype = dbl
         _lib = lib
         return lib
 
@@ -304,6 +341,23 @@ class H2:
     def export(self) -> dict:
         """Every array of the representation, in the layout shared by the
         library's smash_export (documented in include/smash.h)."""
+        e = self.export_structure()
+        lib = _load()
+        nn = self.query("nnodes")
+        for side, tag in ((0, "row"), (1, "col")):
+            e[f"m_{tag}"] = np.empty(nn, np.int32)
+            e[f"k_{tag}"] = np.empty(nn, np.int32)
+            e[f"skel_{tag}"] = np.empty(self.query(f"skel_{tag}"), np.int64)
+            e[f"rest_{tag}"] = np.empty(self.query(f"rest_{tag}"), np.int64)
+            e[f"G_{tag}"] = np.empty(self.query(f"g_{tag}"), np.float64)
+            lib.orc_export_comp(self._h, side, _ptr(e[f"m_{tag}"]), _ptr(e[f"k_{tag}"]),
+                                _ptr(e[f"skel_{tag}"]), _ptr(e[f"rest_{tag}"]), _ptr(e[f"G_{tag}"]))
+        e["swaps_row"] = self.query("swaps_row")
+        e["badswap"] = self.query("badswap")
+        return e
+
+    def export_structure(self) -> dict:
+        """Points, tree and lists (the part shared by every representation)."""
         lib = _load()
         nx, ny, L, nn = (self.query(k) for k in ("nx", "ny", "L", "nnodes"))
         nadm, nnear = self.query("nadm"), self.query("nnear")
@@ -333,14 +387,122 @@ class H2:
         e["near_col"] = np.empty(nnear, np.int32)
         lib.orc_export_lists(self._h, _ptr(e["adm_ptr"]), _ptr(e["adm_col"]), _ptr(e["near_ptr"]),
                              _ptr(e["near_col"]))
-        for side, tag in ((0, "row"), (1, "col")):
-            e[f"m_{tag}"] = np.empty(nn, np.int32)
-            e[f"k_{tag}"] = np.empty(nn, np.int32)
-            e[f"skel_{tag}"] = np.empty(self.query(f"skel_{tag}"), np.int64)
-            e[f"rest_{tag}"] = np.empty(self.query(f"rest_{tag}"), np.int64)
-            e[f"G_{tag}"] = np.empty(self.query(f"g_{tag}"), np.float64)
-            lib.orc_export_comp(self._h, side, _ptr(e[f"m_{tag}"]), _ptr(e[f"k_{tag}"]),
-                                _ptr(e[f"skel_{tag}"]), _ptr(e[f"rest_{tag}"]), _ptr(e[f"G_{tag}"]))
-        e["swaps_row"] = self.query("swaps_row")
-        e["badswap"] = self.query("badswap")
+        return e
+
+
+# --------------------------------------------------------------------------
+# Section 2.1: the Taylor expansion (2.4)-(2.5) of 1/(x - y) on C
+# --------------------------------------------------------------------------
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def cauchy_c(x, y, dx=1.0 + 0.0j) -> complex:
+    """kappa of (2.1) on C: 1/(x - y), d_x where x = y (points as (re, im))."""
+    x, y = _f64(x).ravel(), _f64(y).ravel()
+    im = C.c_double(0.0)
+    re = _load().orc_cauchy_c_entry(_ptr(x), _ptr(y), float(dx.real), float(dx.imag), C.byref(im))
+    return complex(re, im.value)
+
+
+def taylor_coefficients(r: int) -> np.ndarray:
+    """cl[l] = (l/e) (2 pi r)^(1/(2r)), so that eta_{v,l} = (cl[l]/delta_v)^l (2.5)."""
+    cl = np.empty(r)
+    _load().orc_taylor_coefficients(r, _ptr(cl))
+    return cl
+
+
+def taylor_basis_t(pts, r: int, centre: complex, delta: float) -> np.ndarray:
+    """phi_{a,l}(x - a) of (2.5) for l < r at the points (npts x 2, read as
+    x_0 + i x_1): an r x npts complex matrix."""
+    pts = _f64(pts)
+    cl = taylor_coefficients(r)
+    Mt = np.empty((r, len(pts)), np.complex128)
+    _load().orc_taylor_basis_t(r, _ptr(cl), float(centre.real), float(centre.imag), float(delta), _ptr(pts),
+                               len(pts), C.c_void_p(Mt.ctypes.data))
+    return Mt
+
+
+def compr_c(Mt, tol: float, f: float = 2.0):
+    """Complex strong RRQR / ID of the r x m matrix Mt (Theorem 2.4, (2.11)):
+    (perm, k, A, nswaps) with Mt[:, perm[k:]] ~= Mt[:, perm[:k]] @ A."""
+    Mt = _c128(Mt)
+    r, m = Mt.shape
+    perm = np.empty(m, dtype=np.int32)
+    kmax = min(r, m)
+    A = np.zeros(max(kmax * max(m - 1, 0) + 1, 1), np.complex128)
+    k = C.c_int(0)
+    ns = C.c_int(0)
+    _load().orc_compr_c(C.c_void_p(Mt.ctypes.data), r, m, tol, f, _ptr(perm), C.byref(k),
+                        C.c_void_p(A.ctypes.data), C.byref(ns))
+    k = k.value
+    return perm, k, A[: k * (m - k)].reshape(k, m - k).copy(), ns.value
+
+
+def dense_rows_taylor(x, q, rows=None, dx=1.0 + 0.0j) -> np.ndarray:
+    """Brute-force rows of A q for kappa of (2.1) on C (Neumaier sums)."""
+    x = _f64(x)
+    q = _c128(q)
+    if q.ndim == 1:
+        q = q[:, None]
+    nrhs = q.shape[1]
+    rows = np.arange(len(x), dtype=np.int64) if rows is None else np.ascontiguousarray(rows, np.int64)
+    out = np.empty((len(rows), nrhs), np.complex128)
+    _load().orc_dense_rows_taylor(_ptr(x), len(x), C.c_void_p(q.ctypes.data), nrhs, _ptr(rows), len(rows),
+                                  float(dx.real), float(dx.imag), C.c_void_p(out.ctypes.data))
+    return out
+
+
+class H2Taylor(H2):
+    """Oracle H^2 approximation of A = [kappa(x_i, x_j)] with kappa of (2.1)
+    on C (points n x 2 read as x_0 + i x_1, X = Y), bases from the Taylor
+    expansion (2.4) with r terms (Sections 2.1 and 3.3.2)."""
+
+    def __init__(self, x, leaf: int, r: int, tol: float, tau: float = 0.65, f: float = 2.0,
+                 dx: complex = 1.0 + 0.0j):
+        lib = _load()
+        self.x = _f64(x)
+        self.y = None
+        self.d = 2
+        self.kernel, self.leaf, self.order, self.tol, self.tau, self.f = None, leaf, r, tol, tau, f
+        self.r, self.dx = r, complex(dx)
+        h = lib.orc_build_taylor(_ptr(self.x), len(self.x), leaf, r, tau, tol, f, self.dx.real, self.dx.imag)
+        if not h:
+            raise ValueError("oracle: invalid input")
+        self._h = C.c_void_p(h)
+
+    def matvec(self, q) -> np.ndarray:
+        q = _c128(q)
+        squeeze = q.ndim == 1
+        if squeeze:
+            q = q[:, None]
+        q = np.ascontiguousarray(q)
+        z = np.empty((self.query("nx"), q.shape[1]), np.complex128)
+        _load().orc_matvec_taylor(self._h, C.c_void_p(q.ctypes.data), C.c_void_p(z.ctypes.data), q.shape[1], 0)
+        return z[:, 0] if squeeze else z
+
+    def matvec_abs(self, q, leaves=None) -> np.ndarray:
+        """Row scales (sums of |terms|) of the complex matvec."""
+        q = _c128(q)
+        if q.ndim == 1:
+            q = q[:, None]
+        q = np.ascontiguousarray(q)
+        z = np.empty((self.query("nx"), q.shape[1]))
+        _load().orc_matvec_taylor(self._h, C.c_void_p(q.ctypes.data), _ptr(z), q.shape[1], 1)
+        return z
+
+    def matvec_leaves(self, q, leaves):
+        raise NotImplementedError("use matvec() on the Taylor representation")
+
+    def export(self) -> dict:
+        e = super().export_structure()
+        nn = self.query("nnodes")
+        e["m_row"] = np.empty(nn, np.int32)
+        e["k_row"] = np.empty(nn, np.int32)
+        e["skel_row"] = np.empty(self.query("skel_row"), np.int64)
+        e["rest_row"] = np.empty(self.query("rest_row"), np.int64)
+        e["G_row"] = np.empty(self.query("g_row"), np.complex128)
+        _load().orc_export_taylor(self._h, _ptr(e["m_row"]), _ptr(e["k_row"]), _ptr(e["skel_row"]),
+                                  _ptr(e["rest_row"]), C.c_void_p(e["G_row"].ctypes.data))
         return e

@@ -30,6 +30,12 @@
  * Compile with -ffp-contract=off: a*b+c below is two rounded operations unless
  * it is written as fma(a, b, c), the IEEE fused multiply-add (one rounding);
  * the dot products, norms and triangular solves use fma.
+ *
+ * The loops over the nodes of one level, over the nodes of the matvec passes
+ * and over the rows of the dense product carry OpenMP pragmas.  Each
+ * iteration writes only its own node's (or row's) results, so a build with
+ * -fopenmp computes the same bits on several host threads; the default build
+ * ignores the pragmas and runs serially.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,9 +84,10 @@ void orc_dense_rows(const double *x, int64_t nx, const double *y, int64_t ny, in
                     const double *q, int nrhs, const int64_t *rows, int64_t nrows, double *out)
 {
     (void)nx;
-    double *sum = malloc(sizeof(double) * (size_t)nrhs);
-    double *comp = malloc(sizeof(double) * (size_t)nrhs);
+    #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < nrows; ++t) {
+        double *sum = malloc(sizeof(double) * (size_t)nrhs);
+        double *comp = malloc(sizeof(double) * (size_t)nrhs);
         const double *xi = x + rows[t] * d;
         for (int c = 0; c < nrhs; ++c) { sum[c] = 0.0; comp[c] = 0.0; }
         for (int64_t j = 0; j < ny; ++j) {
@@ -97,9 +104,9 @@ void orc_dense_rows(const double *x, int64_t nx, const double *y, int64_t ny, in
         }
         for (int c = 0; c < nrhs; ++c)
             out[t * nrhs + c] = sum[c] + comp[c];
+        free(sum);
+        free(comp);
     }
-    free(sum);
-    free(comp);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -499,6 +506,13 @@ typedef struct orc_h2 {
     int32_t *adm_col, *near_col;
     int64_t nadm, nnear;
     orc_comp *rowc, *colc;
+    /* the Taylor-expansion representation of 1/(x - y) on C (Section 2.1):
+     * rt terms, coefficients cl[l] = (l/e)(2 pi rt)^(1/(2 rt)) of (2.5), the
+     * diagonal value d_x of (2.1); G of every node is complex, (m-k) x k
+     * interleaved (re, im) */
+    int cplx, rt;
+    double cl[ORC_MAXP];
+    double dx_re, dx_im;
 } orc_h2;
 
 /* growable pair list */
@@ -685,6 +699,7 @@ static void orc_compress_node(orc_h2 *h, int g, int side)
 }
 
 void orc_free(orc_h2 *h);
+static void orc_structure(orc_h2 *h, const double *x, int64_t nx, const double *y, int64_t ny);
 
 /* Build: returns NULL on invalid input.  y == NULL means Y = X. */
 orc_h2 *orc_build(const double *x, int64_t nx, const double *y, int64_t ny, int d, int kid,
@@ -702,10 +717,29 @@ orc_h2 *orc_build(const double *x, int64_t nx, const double *y, int64_t ny, int 
     h->d = d; h->kid = kid; h->leaf = leaf; h->p = p; h->tau = tau; h->tol = tol; h->f = f;
     h->r = 1;
     for (int a = 0; a < d; ++a) h->r *= p;
+    orc_chebyshev(p, h->anchors);
+    orc_structure(h, x, nx, y, ny);
+    h->rowc = calloc((size_t)h->nnodes, sizeof(orc_comp));
+    h->colc = h->same ? h->rowc : calloc((size_t)h->nnodes, sizeof(orc_comp));
+    /* (3.16)-(3.18): levels L..2, bottom-up */
+    for (int l = h->L; l >= 2; --l) {
+        #pragma omp parallel for schedule(dynamic)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            orc_compress_node(h, (int)g, 0);
+            if (!h->same) orc_compress_node(h, (int)g, 1);
+        }
+    }
+    return h;
+}
+
+/* Sections 3.1 and 3.2: bounding cube, sorted points, the adaptive tree and
+ * the lists L (3.3) and L^- (3.4), for h->d, h->leaf and h->tau. */
+static void orc_structure(orc_h2 *h, const double *x, int64_t nx, const double *y, int64_t ny)
+{
+    int d = h->d;
     h->same = (y == NULL);
     h->nx = nx; h->ny = y ? ny : nx;
     h->b = orc_bits_per_dim(d);
-    orc_chebyshev(p, h->anchors);
     orc_bounding_cube(x, nx, y, ny, d, h->lo, &h->s);
     h->permx = malloc(sizeof(int64_t) * (size_t)nx);
     h->keyx = malloc(sizeof(uint64_t) * (size_t)nx);
@@ -726,15 +760,6 @@ orc_h2 *orc_build(const double *x, int64_t nx, const double *y, int64_t ny, int 
     orc_to_csr(h->nnodes, &adm, &h->adm_ptr, &h->adm_col);
     orc_to_csr(h->nnodes, &near, &h->near_ptr, &h->near_col);
     free(adm.v); free(near.v);
-    h->rowc = calloc((size_t)h->nnodes, sizeof(orc_comp));
-    h->colc = h->same ? h->rowc : calloc((size_t)h->nnodes, sizeof(orc_comp));
-    /* (3.16)-(3.18): levels L..2, bottom-up */
-    for (int l = h->L; l >= 2; --l)
-        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
-            orc_compress_node(h, (int)g, 0);
-            if (!h->same) orc_compress_node(h, (int)g, 1);
-        }
-    return h;
 }
 
 static void orc_free_comp(orc_comp *c, int n)
@@ -784,7 +809,8 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
     double **qhat = calloc((size_t)h->nnodes, sizeof(double *));
     double **zhat = calloc((size_t)h->nnodes, sizeof(double *));
     /* step 1: upward pass, q^_i = V_i^T q|_i at leaves, sum_c W_c^T q^_c above */
-    for (int l = h->L; l >= 2; --l)
+    for (int l = h->L; l >= 2; --l) {
+        #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
             const orc_node *nd = &h->nodes[g];
             const orc_comp *cp = &h->colc[g];
@@ -810,7 +836,9 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
                 }
             free(in);
         }
+    }
     /* step 2: coupling, z^_i = sum_{(i,j) in L} A|_{i^ x j^} q^_j  (3.19) */
+    #pragma omp parallel for schedule(dynamic, 16)
     for (int g = 0; g < h->nnodes; ++g) {
         const orc_comp *ci = &h->rowc[g];
         zhat[g] = calloc((size_t)(ci->k > 0 ? ci->k : 1) * nrhs, sizeof(double));
@@ -829,7 +857,8 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
         }
     }
     /* step 3: downward pass, z^_c += R_c z^_i, and z|_i = U_i z^_i at leaves */
-    for (int l = 2; l <= h->L; ++l)
+    for (int l = 2; l <= h->L; ++l) {
+        #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
             if (need && !need[g]) continue;
             const orc_node *nd = &h->nodes[g];
@@ -859,7 +888,9 @@ static int orc_matvec_masked(const orc_h2 *h, const double *q, double *z, int nr
             }
             free(out);
         }
+    }
     /* near field (3.20): z|_i += A|_{i x j} q|_j for (i,j) in L^- */
+    #pragma omp parallel for schedule(dynamic, 16)
     for (int g = 0; g < h->nnodes; ++g) {
         if (need && !need[g]) continue;
         const orc_node *ni = &h->nodes[g];
@@ -1028,3 +1059,538 @@ void orc_export_comp(const orc_h2 *h, int side, int32_t *m, int32_t *k, int64_t 
         for (int64_t e = 0; e < (int64_t)mk * c[g].k; ++e) G[pg++] = c[g].G[e];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Section 2.1: the Taylor expansion (2.4)-(2.5) of 1/(x - y) on C, and the  */
+/* H^2 construction (3.16)-(3.20) and matvec (Section 3.4) built on it       */
+/* ------------------------------------------------------------------------ */
+/* Points are complex numbers x = x_0 + i x_1 (d = 2).  Complex values are
+ * pairs of doubles and every operation is written out in real arithmetic, so
+ * the order of the roundings is the one written here. */
+
+typedef struct { double re, im; } orc_cx;
+
+static orc_cx cx_mul(orc_cx a, orc_cx b)
+{
+    orc_cx c = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+    return c;
+}
+
+/* a * conj(b) */
+static orc_cx cx_mulc(orc_cx a, orc_cx b)
+{
+    orc_cx c = {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+    return c;
+}
+
+static orc_cx cx_div(orc_cx a, orc_cx b)
+{
+    double den = b.re * b.re + b.im * b.im;
+    orc_cx c = {(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+    return c;
+}
+
+static double cx_abs2(orc_cx a) { return fma(a.re, a.re, a.im * a.im); }
+
+/* kappa of (2.1): 1/(x - y) for x != y, d_x where the points coincide */
+static orc_cx orc_cauchy_c(const double *x, const double *y, double dx_re, double dx_im)
+{
+    orc_cx t = {x[0] - y[0], x[1] - y[1]};
+    if (t.re == 0.0 && t.im == 0.0) {
+        orc_cx dv = {dx_re, dx_im};
+        return dv;
+    }
+    double den = t.re * t.re + t.im * t.im;
+    orc_cx v = {t.re / den, -t.im / den};
+    return v;
+}
+
+double orc_cauchy_c_entry(const double *x, const double *y, double dx_re, double dx_im, double *out_im)
+{
+    orc_cx v = orc_cauchy_c(x, y, dx_re, dx_im);
+    *out_im = v.im;
+    return v.re;
+}
+
+/* The factors of (2.5) that do not depend on the node:
+ * cl[l] = (l/e) (2 pi r)^(1/(2r)), so that eta_{v,l} = (cl[l] / delta_v)^l. */
+void orc_taylor_coefficients(int r, double *cl)
+{
+    double rho = pow(2.0 * ORC_PI * (double)r, 1.0 / (2.0 * (double)r));
+    for (int l = 0; l < r; ++l) cl[l] = ((double)l / exp(1.0)) * rho;
+}
+
+/* phi_{a,l}(x - a) = eta_{a,l} (x - a)^l / l!  of (2.5), l = 0..r-1, at npts
+ * points (pts: npts x 2), as the rows of Mt (r x npts complex, interleaved):
+ * with u = (x - a)/delta and w = cl[l] u, phi_l = w^l / l!, formed as l
+ * steps v <- (v w) / j. */
+void orc_taylor_basis_t(int r, const double *cl, double a_re, double a_im, double delta, const double *pts,
+                        int npts, double *Mt)
+{
+    for (int c = 0; c < npts; ++c) {
+        orc_cx u = {(pts[2 * c] - a_re) / delta, (pts[2 * c + 1] - a_im) / delta};
+        for (int l = 0; l < r; ++l) {
+            orc_cx w = {cl[l] * u.re, cl[l] * u.im};
+            orc_cx v = {1.0, 0.0};
+            for (int j = 1; j <= l; ++j) {
+                v = cx_mul(v, w);
+                v.re = v.re / (double)j;
+                v.im = v.im / (double)j;
+            }
+            Mt[2 * ((size_t)l * npts + c)] = v.re;
+            Mt[2 * ((size_t)l * npts + c) + 1] = v.im;
+        }
+    }
+}
+
+/* Complex Householder step on column j of W (r x m complex, row-major),
+ * in the convention of LAPACK's elementary reflectors: H = I - tau v v^H
+ * with v_j = 1 and real beta, H^H [alpha; x] = [beta; 0],
+ * beta = -sign(Re alpha) sqrt(|alpha|^2 + |x|^2), tau = (beta - alpha)/beta,
+ * v = x / (alpha - beta); H^H is applied to the columns j+1..m-1. */
+static void orc_householder_c(orc_cx *W, int r, int m, int j, orc_cx *v)
+{
+    orc_cx alpha = W[(size_t)j * m + j];
+    double sigma = 0.0;
+    for (int i = j + 1; i < r; ++i) {
+        orc_cx x = W[(size_t)i * m + j];
+        sigma = fma(x.re, x.re, sigma);
+        sigma = fma(x.im, x.im, sigma);
+    }
+    if (sigma == 0.0 && alpha.im == 0.0)
+        return; /* already triangular with a real diagonal entry: H = I */
+    double nrm = sqrt(fma(alpha.re, alpha.re, fma(alpha.im, alpha.im, sigma)));
+    double beta = alpha.re <= 0.0 ? nrm : -nrm;
+    orc_cx tau = {(beta - alpha.re) / beta, -alpha.im / beta};
+    orc_cx den = {alpha.re - beta, alpha.im};
+    v[j].re = 1.0; v[j].im = 0.0;
+    for (int i = j + 1; i < r; ++i) v[i] = cx_div(W[(size_t)i * m + j], den);
+    for (int c = j + 1; c < m; ++c) {
+        /* w = v^H W[:, c] */
+        orc_cx w = W[(size_t)j * m + c];
+        for (int i = j + 1; i < r; ++i) {
+            orc_cx x = W[(size_t)i * m + c];
+            w.re = fma(v[i].re, x.re, fma(v[i].im, x.im, w.re));
+            w.im = fma(v[i].re, x.im, fma(-v[i].im, x.re, w.im));
+        }
+        /* W[:, c] -= conj(tau) w v */
+        orc_cx tw = cx_mulc(w, tau);
+        W[(size_t)j * m + c].re = W[(size_t)j * m + c].re - tw.re;
+        W[(size_t)j * m + c].im = W[(size_t)j * m + c].im - tw.im;
+        for (int i = j + 1; i < r; ++i) {
+            orc_cx y = cx_mul(tw, v[i]);
+            W[(size_t)i * m + c].re = W[(size_t)i * m + c].re - y.re;
+            W[(size_t)i * m + c].im = W[(size_t)i * m + c].im - y.im;
+        }
+    }
+    W[(size_t)j * m + j].re = beta;
+    W[(size_t)j * m + j].im = 0.0;
+    for (int i = j + 1; i < r; ++i) { W[(size_t)i * m + j].re = 0.0; W[(size_t)i * m + j].im = 0.0; }
+}
+
+/* Complex counterpart of orc_qr: pivot on the largest remaining column norm
+ * (ties: lowest position), rank cut |R_jj| <= tol |R_00|. */
+static int orc_qr_c(orc_cx *W, int r, int m, int *perm, int pivot, int ksteps, double tol, double *nrm2,
+                    orc_cx *v)
+{
+    int kmax = pivot ? (r < m ? r : m) : ksteps;
+    double r00 = 0.0;
+    for (int j = 0; j < kmax; ++j) {
+        if (pivot) {
+            for (int c = j; c < m; ++c) {
+                double s2 = 0.0;
+                for (int i = j; i < r; ++i) {
+                    orc_cx x = W[(size_t)i * m + c];
+                    s2 = fma(x.re, x.re, s2);
+                    s2 = fma(x.im, x.im, s2);
+                }
+                nrm2[c] = s2;
+            }
+            int piv = j;
+            for (int c = j + 1; c < m; ++c)
+                if (nrm2[c] > nrm2[piv]) piv = c;
+            double nrm = sqrt(nrm2[piv]);
+            if (j == 0) {
+                r00 = nrm;
+                if (nrm == 0.0) return 0;
+            } else if (nrm <= tol * r00) {
+                return j;
+            }
+            if (piv != j) {
+                for (int i = 0; i < r; ++i) {
+                    orc_cx t = W[(size_t)i * m + j];
+                    W[(size_t)i * m + j] = W[(size_t)i * m + piv];
+                    W[(size_t)i * m + piv] = t;
+                }
+                int tp = perm[j]; perm[j] = perm[piv]; perm[piv] = tp;
+            }
+        }
+        orc_householder_c(W, r, m, j, v);
+    }
+    return kmax;
+}
+
+/* compr (2.14) on a complex Mt (r x m, interleaved): Theorem 2.4 with the
+ * same steps as orc_compr; A = R11^{-1} R12 (k x (m-k), interleaved). */
+int orc_compr_c(const double *Mt_in, int r, int m, double tol, double f, int *perm, int *k_out, double *A_out,
+                int *nswaps_out)
+{
+    const orc_cx *Mt = (const orc_cx *)Mt_in;
+    orc_cx *A = (orc_cx *)A_out;
+    orc_cx *W = malloc(sizeof(orc_cx) * (size_t)r * (size_t)(m > 0 ? m : 1));
+    double *nrm2 = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    orc_cx *v = malloc(sizeof(orc_cx) * (size_t)(r > 0 ? r : 1));
+    for (int c = 0; c < m; ++c) perm[c] = c;
+    memcpy(W, Mt, sizeof(orc_cx) * (size_t)r * (size_t)m);
+    int k = orc_qr_c(W, r, m, perm, 1, 0, tol, nrm2, v);
+    int nsw = 0;
+    int mk = m - k;
+    orc_cx *X = malloc(sizeof(orc_cx) * (size_t)(k > 0 ? k * k : 1));
+    double *rho = malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    double *g2 = malloc(sizeof(double) * (size_t)(mk > 0 ? mk : 1));
+    for (;;) {
+        if (k == 0 || mk == 0) break;
+        /* A = R11^{-1} R12 by back substitution, one column at a time */
+        for (int u = 0; u < mk; ++u)
+            for (int t = k - 1; t >= 0; --t) {
+                orc_cx s = W[(size_t)t * m + k + u];
+                for (int q = t + 1; q < k; ++q) {
+                    orc_cx y = cx_mul(W[(size_t)t * m + q], A[(size_t)q * mk + u]);
+                    s.re = s.re - y.re;
+                    s.im = s.im - y.im;
+                }
+                A[(size_t)t * mk + u] = cx_div(s, W[(size_t)t * m + t]);
+            }
+        /* X = R11^{-1}; 1/omega_t^2 = squared norm of row t of X */
+        for (int c = 0; c < k; ++c)
+            for (int t = k - 1; t >= 0; --t) {
+                orc_cx s = {(t == c) ? 1.0 : 0.0, 0.0};
+                for (int q = t + 1; q < k; ++q) {
+                    orc_cx y = cx_mul(W[(size_t)t * m + q], X[(size_t)q * k + c]);
+                    s.re = s.re - y.re;
+                    s.im = s.im - y.im;
+                }
+                X[(size_t)t * k + c] = cx_div(s, W[(size_t)t * m + t]);
+            }
+        for (int t = 0; t < k; ++t) {
+            double s = 0.0;
+            for (int c = 0; c < k; ++c) {
+                s = fma(X[(size_t)t * k + c].re, X[(size_t)t * k + c].re, s);
+                s = fma(X[(size_t)t * k + c].im, X[(size_t)t * k + c].im, s);
+            }
+            rho[t] = s;
+        }
+        /* gamma_u^2 = squared norm of column u of R22 */
+        for (int u = 0; u < mk; ++u) {
+            double s = 0.0;
+            for (int i = k; i < r; ++i) {
+                s = fma(W[(size_t)i * m + k + u].re, W[(size_t)i * m + k + u].re, s);
+                s = fma(W[(size_t)i * m + k + u].im, W[(size_t)i * m + k + u].im, s);
+            }
+            g2[u] = s;
+        }
+        double best = -1.0;
+        int bt = 0, bu = 0;
+        for (int t = 0; t < k; ++t)
+            for (int u = 0; u < mk; ++u) {
+                orc_cx a = A[(size_t)t * mk + u];
+                double val = fma(a.re, a.re, fma(a.im, a.im, g2[u] * rho[t]));
+                if (val > best) { best = val; bt = t; bu = u; }
+            }
+        if (best <= f * f) break;
+        if (nsw >= ORC_MAX_SWAPS) { nsw = -1; break; }
+        int tp = perm[bt]; perm[bt] = perm[k + bu]; perm[k + bu] = tp;
+        ++nsw;
+        for (int i = 0; i < r; ++i)
+            for (int c = 0; c < m; ++c)
+                W[(size_t)i * m + c] = Mt[(size_t)i * m + perm[c]];
+        orc_qr_c(W, r, m, perm, 0, k, tol, nrm2, v);
+    }
+    *k_out = k;
+    *nswaps_out = nsw;
+    free(W); free(nrm2); free(v); free(X); free(rho); free(g2);
+    return 0;
+}
+
+/* (3.16)-(3.18) for one node with the Taylor basis of its cell: centre a =
+ * the cell centre, radius delta = half the cell diagonal (Definition 2.1 on
+ * the cell, as (4.6) does). */
+static void orc_compress_node_c(orc_h2 *h, int g)
+{
+    orc_node *nd = &h->nodes[g];
+    orc_comp *cp = &h->rowc[g];
+    int r = h->rt;
+    int m;
+    if (nd->leaf) {
+        m = (int)nd->rc;
+        cp->ibar = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        for (int c = 0; c < m; ++c) cp->ibar[c] = nd->rs + c;
+    } else {
+        m = 0;
+        for (int c = 0; c < nd->nchild; ++c) m += h->rowc[nd->child0 + c].k;
+        cp->ibar = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        int pos = 0;
+        for (int c = 0; c < nd->nchild; ++c) {
+            orc_comp *ch = &h->rowc[nd->child0 + c];
+            for (int t = 0; t < ch->k; ++t) cp->ibar[pos++] = ch->skel[t];
+        }
+    }
+    cp->m = m;
+    if (m == 0) { cp->k = 0; return; }
+    double hc = ldexp(h->s, 1 - nd->level);
+    double a_re = h->lo[0] + ((double)nd->cell[0] + 0.5) * hc;
+    double a_im = h->lo[1] + ((double)nd->cell[1] + 0.5) * hc;
+    double delta = 0.5 * hc * sqrt(2.0);
+    double *P = malloc(sizeof(double) * (size_t)m * 2);
+    for (int c = 0; c < m; ++c) { P[2 * c] = h->xs[cp->ibar[c] * 2]; P[2 * c + 1] = h->xs[cp->ibar[c] * 2 + 1]; }
+    double *Mt = malloc(sizeof(double) * 2 * (size_t)r * (size_t)m);
+    orc_taylor_basis_t(r, h->cl, a_re, a_im, delta, P, m, Mt);
+    int *perm = malloc(sizeof(int) * (size_t)m);
+    int kmax = r < m ? r : m;
+    double *A = malloc(sizeof(double) * 2 * (size_t)(kmax * (m - 1) + 1));
+    int k, nsw;
+    orc_compr_c(Mt, r, m, h->tol, h->f, perm, &k, A, &nsw);
+    cp->k = k;
+    cp->nswaps = nsw;
+    int *sel = calloc((size_t)m, sizeof(int));
+    for (int t = 0; t < k; ++t) sel[perm[t]] = 1;
+    int *rank = malloc(sizeof(int) * (size_t)m);
+    int ns = 0, nr = 0;
+    for (int pos = 0; pos < m; ++pos) rank[pos] = sel[pos] ? ns++ : nr++;
+    cp->skel = malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest = malloc(sizeof(int64_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->skel_loc = malloc(sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest_loc = malloc(sizeof(int32_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->G = malloc(sizeof(double) * 2 * (size_t)((m - k) * k > 0 ? (m - k) * k : 1));
+    for (int pos = 0; pos < m; ++pos) {
+        if (sel[pos]) { cp->skel[rank[pos]] = cp->ibar[pos]; cp->skel_loc[rank[pos]] = pos; }
+        else { cp->rest[rank[pos]] = cp->ibar[pos]; cp->rest_loc[rank[pos]] = pos; }
+    }
+    int mk = m - k;
+    for (int t = 0; t < k; ++t)
+        for (int u = 0; u < mk; ++u) {
+            size_t dst = (size_t)rank[perm[k + u]] * k + rank[perm[t]];
+            cp->G[2 * dst] = A[2 * ((size_t)t * mk + u)];
+            cp->G[2 * dst + 1] = A[2 * ((size_t)t * mk + u) + 1];
+        }
+    free(P); free(Mt); free(perm); free(A); free(sel); free(rank);
+}
+
+/* H^2 approximation of A = [kappa(x_i, x_j)] with kappa of (2.1) on C (X = Y,
+ * points n x 2 read as x_0 + i x_1), bases from the Taylor expansion (2.4)
+ * with r terms, separation ratio tau, rank cut tol, SRRQR bound f.  Returns
+ * NULL on invalid input. */
+orc_h2 *orc_build_taylor(const double *x, int64_t n, int leaf, int r, double tau, double tol, double f,
+                         double dx_re, double dx_im)
+{
+    if (n < 1 || leaf < 1 || r < 1 || r > ORC_MAXP || !(tol > 0.0) || !(tau > 0.0 && tau < 1.0) || !(f > 1.0))
+        return NULL;
+    for (int64_t i = 0; i < n * 2; ++i) if (!isfinite(x[i])) return NULL;
+    orc_h2 *h = calloc(1, sizeof(orc_h2));
+    h->d = 2; h->kid = -1; h->leaf = leaf; h->p = 0; h->r = r; h->tau = tau; h->tol = tol; h->f = f;
+    h->cplx = 1; h->rt = r; h->dx_re = dx_re; h->dx_im = dx_im;
+    orc_taylor_coefficients(r, h->cl);
+    orc_structure(h, x, n, NULL, 0);
+    h->rowc = calloc((size_t)h->nnodes, sizeof(orc_comp));
+    h->colc = h->rowc;
+    for (int l = h->L; l >= 2; --l) {
+        #pragma omp parallel for schedule(dynamic)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) orc_compress_node_c(h, (int)g);
+    }
+    return h;
+}
+
+/* Section 3.4 on the complex representation: z = A^ q with q, z n x nrhs
+ * complex (interleaved), in the caller's order.  Steps as in
+ * orc_matvec_masked (upward with [I G^T] P^T, coupling (3.19), downward,
+ * near field (3.20) with kappa(x, x) = d_x); absval != 0 replaces every factor
+ * by its magnitude and writes real row scales to z (n x nrhs doubles). */
+int orc_matvec_taylor(const orc_h2 *h, const double *q_in, double *z_out, int nrhs, int absval)
+{
+    if (!h->cplx) return -1;
+    int64_t n = h->nx;
+    const orc_cx *q = (const orc_cx *)q_in;
+    orc_cx *qs = malloc(sizeof(orc_cx) * (size_t)n * nrhs);
+    orc_cx *zs = calloc((size_t)n * nrhs, sizeof(orc_cx));
+    for (int64_t pnt = 0; pnt < n; ++pnt)
+        for (int c = 0; c < nrhs; ++c) {
+            orc_cx v = q[h->permx[pnt] * nrhs + c];
+            if (absval) { v.re = sqrt(cx_abs2(v)); v.im = 0.0; }
+            qs[pnt * nrhs + c] = v;
+        }
+    orc_cx **qhat = calloc((size_t)h->nnodes, sizeof(orc_cx *));
+    orc_cx **zhat = calloc((size_t)h->nnodes, sizeof(orc_cx *));
+#define ORC_GC(cp, idx) (absval ? (orc_cx){sqrt(cx_abs2(((const orc_cx *)(cp)->G)[idx])), 0.0} \
+                                : ((const orc_cx *)(cp)->G)[idx])
+    for (int l = h->L; l >= 2; --l) {
+        #pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            const orc_node *nd = &h->nodes[g];
+            const orc_comp *cp = &h->rowc[g];
+            int m = cp->m, k = cp->k;
+            orc_cx *in = malloc(sizeof(orc_cx) * (size_t)(m > 0 ? m : 1) * nrhs);
+            if (nd->leaf) {
+                memcpy(in, qs + nd->rs * nrhs, sizeof(orc_cx) * (size_t)m * nrhs);
+            } else {
+                int pos = 0;
+                for (int c = 0; c < nd->nchild; ++c) {
+                    int kc = h->rowc[nd->child0 + c].k;
+                    memcpy(in + (size_t)pos * nrhs, qhat[nd->child0 + c], sizeof(orc_cx) * (size_t)kc * nrhs);
+                    pos += kc;
+                }
+            }
+            qhat[g] = calloc((size_t)(k > 0 ? k : 1) * nrhs, sizeof(orc_cx));
+            for (int t = 0; t < k; ++t)
+                for (int c = 0; c < nrhs; ++c) {
+                    orc_cx s = in[(size_t)cp->skel_loc[t] * nrhs + c];
+                    for (int u = 0; u < m - k; ++u) {
+                        orc_cx y = cx_mul(ORC_GC(cp, (size_t)u * k + t), in[(size_t)cp->rest_loc[u] * nrhs + c]);
+                        s.re = s.re + y.re;
+                        s.im = s.im + y.im;
+                    }
+                    qhat[g][(size_t)t * nrhs + c] = s;
+                }
+            free(in);
+        }
+    }
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_comp *ci = &h->rowc[g];
+        zhat[g] = calloc((size_t)(ci->k > 0 ? ci->k : 1) * nrhs, sizeof(orc_cx));
+        for (int64_t e = h->adm_ptr[g]; e < h->adm_ptr[g + 1]; ++e) {
+            int j = h->adm_col[e];
+            const orc_comp *cj = &h->rowc[j];
+            for (int a = 0; a < ci->k; ++a)
+                for (int bb = 0; bb < cj->k; ++bb) {
+                    orc_cx kv = orc_cauchy_c(h->xs + ci->skel[a] * 2, h->xs + cj->skel[bb] * 2, h->dx_re, h->dx_im);
+                    if (absval) { kv.re = sqrt(cx_abs2(kv)); kv.im = 0.0; }
+                    for (int c = 0; c < nrhs; ++c) {
+                        orc_cx y = cx_mul(kv, qhat[j][(size_t)bb * nrhs + c]);
+                        zhat[g][(size_t)a * nrhs + c].re += y.re;
+                        zhat[g][(size_t)a * nrhs + c].im += y.im;
+                    }
+                }
+        }
+    }
+    for (int l = 2; l <= h->L; ++l) {
+        #pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            const orc_node *nd = &h->nodes[g];
+            const orc_comp *cp = &h->rowc[g];
+            int m = cp->m, k = cp->k;
+            orc_cx *out = calloc((size_t)(m > 0 ? m : 1) * nrhs, sizeof(orc_cx));
+            for (int t = 0; t < k; ++t)
+                for (int c = 0; c < nrhs; ++c)
+                    out[(size_t)cp->skel_loc[t] * nrhs + c] = zhat[g][(size_t)t * nrhs + c];
+            for (int u = 0; u < m - k; ++u)
+                for (int c = 0; c < nrhs; ++c) {
+                    orc_cx s = {0.0, 0.0};
+                    for (int t = 0; t < k; ++t) {
+                        orc_cx y = cx_mul(ORC_GC(cp, (size_t)u * k + t), zhat[g][(size_t)t * nrhs + c]);
+                        s.re = s.re + y.re;
+                        s.im = s.im + y.im;
+                    }
+                    out[(size_t)cp->rest_loc[u] * nrhs + c] = s;
+                }
+            if (nd->leaf) {
+                for (int64_t a = 0; a < (int64_t)m * nrhs; ++a) {
+                    zs[nd->rs * nrhs + a].re += out[a].re;
+                    zs[nd->rs * nrhs + a].im += out[a].im;
+                }
+            } else {
+                int pos = 0;
+                for (int c = 0; c < nd->nchild; ++c) {
+                    int kc = h->rowc[nd->child0 + c].k;
+                    for (int64_t a = 0; a < (int64_t)kc * nrhs; ++a) {
+                        zhat[nd->child0 + c][a].re += out[(size_t)pos * nrhs + a].re;
+                        zhat[nd->child0 + c][a].im += out[(size_t)pos * nrhs + a].im;
+                    }
+                    pos += kc;
+                }
+            }
+            free(out);
+        }
+    }
+#undef ORC_GC
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_node *ni = &h->nodes[g];
+        for (int64_t e = h->near_ptr[g]; e < h->near_ptr[g + 1]; ++e) {
+            const orc_node *nj = &h->nodes[h->near_col[e]];
+            for (int64_t a = ni->rs; a < ni->rs + ni->rc; ++a)
+                for (int64_t bb = nj->cs; bb < nj->cs + nj->cc; ++bb) {
+                    orc_cx kv = orc_cauchy_c(h->xs + a * 2, h->xs + bb * 2, h->dx_re, h->dx_im);
+                    if (absval) { kv.re = sqrt(cx_abs2(kv)); kv.im = 0.0; }
+                    for (int c = 0; c < nrhs; ++c) {
+                        orc_cx y = cx_mul(kv, qs[bb * nrhs + c]);
+                        zs[a * nrhs + c].re += y.re;
+                        zs[a * nrhs + c].im += y.im;
+                    }
+                }
+        }
+    }
+    for (int64_t pnt = 0; pnt < n; ++pnt)
+        for (int c = 0; c < nrhs; ++c) {
+            orc_cx v = zs[pnt * nrhs + c];
+            if (absval) {
+                z_out[h->permx[pnt] * nrhs + c] = v.re;
+            } else {
+                z_out[2 * (h->permx[pnt] * nrhs + c)] = v.re;
+                z_out[2 * (h->permx[pnt] * nrhs + c) + 1] = v.im;
+            }
+        }
+    for (int g = 0; g < h->nnodes; ++g) { free(qhat[g]); free(zhat[g]); }
+    free(qhat); free(zhat); free(qs); free(zs);
+    return 0;
+}
+
+/* Dense rows of A q for kappa of (2.1) on C (Neumaier-compensated sums of
+ * the real and imaginary parts): out[t] = sum_j kappa(x_rows[t], x_j) q_j. */
+void orc_dense_rows_taylor(const double *x, int64_t n, const double *q_in, int nrhs, const int64_t *rows,
+                           int64_t nrows, double dx_re, double dx_im, double *out)
+{
+    const orc_cx *q = (const orc_cx *)q_in;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < nrows; ++t) {
+        double *sum = calloc((size_t)2 * nrhs, sizeof(double));
+        double *comp = calloc((size_t)2 * nrhs, sizeof(double));
+        for (int64_t j = 0; j < n; ++j) {
+            orc_cx kv = orc_cauchy_c(x + rows[t] * 2, x + j * 2, dx_re, dx_im);
+            for (int c = 0; c < nrhs; ++c) {
+                orc_cx y = cx_mul(kv, q[j * nrhs + c]);
+                double parts[2] = {y.re, y.im};
+                for (int p = 0; p < 2; ++p) {
+                    double *sm = &sum[2 * c + p], *cm = &comp[2 * c + p];
+                    double v = parts[p];
+                    double s2 = *sm + v;
+                    if (fabs(*sm) >= fabs(v)) *cm += (*sm - s2) + v;
+                    else *cm += (v - s2) + *sm;
+                    *sm = s2;
+                }
+            }
+        }
+        for (int c = 0; c < nrhs; ++c) {
+            out[2 * (t * nrhs + c)] = sum[2 * c] + comp[2 * c];
+            out[2 * (t * nrhs + c) + 1] = sum[2 * c + 1] + comp[2 * c + 1];
+        }
+        free(sum);
+        free(comp);
+    }
+}
+
+/* Per node (gid order): m, k, skeleton and rest indices (sorted positions)
+ * and the complex G ((m-k) x k interleaved) of the Taylor representation. */
+void orc_export_taylor(const orc_h2 *h, int32_t *m, int32_t *k, int64_t *skel, int64_t *rest, double *G)
+{
+    int64_t ps = 0, pr = 0, pg = 0;
+    for (int g = 0; g < h->nnodes; ++g) {
+        const orc_comp *c = &h->rowc[g];
+        m[g] = c->m; k[g] = c->k;
+        for (int t = 0; t < c->k; ++t) skel[ps++] = c->skel[t];
+        for (int u = 0; u < c->m - c->k; ++u) rest[pr++] = c->rest[u];
+        int64_t ng = (int64_t)(c->m - c->k) * c->k;
+        if (ng > 0) memcpy(G + 2 * pg, c->G, sizeof(double) * 2 * (size_t)ng);
+        pg += ng;
+    }
+}
+

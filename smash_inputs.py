@@ -29,6 +29,8 @@ __all__ = [
     "batched_problems",
     "WORKLOADS",
     "make_workload",
+    "grid_2d",
+    "uniform_01",
 ]
 
 
@@ -151,6 +153,19 @@ def jittered_grid(cells_per_dim: int, d: int, seed: int, per_cell: int = 1) -> n
     pts[-1] = 1.0 - 2.0 ** -40
     pts = pts[g.permutation(len(pts))]
     return np.ascontiguousarray(pts, dtype=np.float64)
+
+
+def grid_2d(m: int) -> np.ndarray:
+    """The uniform m x m grid of Section 6.2 in [0,1]^2: points ((i + 1/2)/m,
+    (j + 1/2)/m), j fastest, shape (m*m, 2)."""
+    t = (np.arange(m, dtype=np.float64) + 0.5) / m
+    gx, gy = np.meshgrid(t, t, indexing="ij")
+    return np.ascontiguousarray(np.stack([gx.ravel(), gy.ravel()], axis=1))
+
+
+def uniform_01(n: int, nrhs: int, seed: int) -> np.ndarray:
+    """n x nrhs entries U[0,1] (the rand([0,1]) vectors of Section 6.2)."""
+    return np.ascontiguousarray(_rng(seed).random((n, nrhs)), dtype=np.float64)
 
 
 def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
