@@ -28,6 +28,13 @@ Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
   complex H^2 matvec ....... pinned (dense when the root is a leaf,
                              antisymmetry of 1/(x-y), error falling with r,
                              the error magnitudes of Table 6.1)
+  Jacobi truncated SVD ..... pinned (singular values and subspaces of
+                             LAPACK's SVD, orthogonality)
+  HSS construction ......... pinned (exact cover by (3.5), the bound on
+                             |N_i| and the empty third case of Appendix A
+                             for uniform points, dense when the root is a
+                             leaf, |G| <= f, error falling with eps_svd,
+                             antisymmetry of 1/(x-y))
 """
 from __future__ import annotations
 
@@ -54,7 +61,7 @@ KERNEL_DLP1, KERNEL_DLP2 = 4, 5  # y-gradient of -(1/2 pi) log|x - y| (Section 6
 
 _Q = dict(nx=0, ny=1, L=2, nnodes=3, nadm=4, nnear=5, same=6, skel_row=7, rest_row=8,
           g_row=9, skel_col=10, rest_col=11, g_col=12, r=13, swaps_row=14, swaps_col=15,
-          badswap=16)
+          badswap=16, nnf=17)
 
 
 def _compile(path: str, extra, force: bool) -> str:
@@ -147,6 +154,14 @@ def _load():
         lib.orc_dense_rows_taylor.restype = None
         lib.orc_export_taylor.argtypes = [P] * 6
         lib.orc_export_taylor.restype = None
+        lib.orc_build_hss.restype = P
+        lib.orc_build_hss.argtypes = [P, i64, P, i64, i32, i32, i32, dbl, dbl, dbl, dbl]
+        lib.orc_export_hss.argtypes = [P, P, P, P, P]
+        lib.orc_export_hss.restype = None
+        lib.orc_jacobi_rows.argtypes = [P, i32, i32, P, P]
+        lib.orc_jacobi_rows.restype = i32
+        lib.orc_truncated_svd_rows.argtypes = [P, i32, i32, dbl, P]
+        lib.orc_truncated_svd_rows.restype = i32
         lib.orc_cauchy_c_entry.argtypes = [P, P, dbl, dbl, P]
         lib.orc_cauchy_c_entry.restype = dbl
         _lib = lib
@@ -505,4 +520,65 @@ class H2Taylor(H2):
         e["G_row"] = np.empty(self.query("g_row"), np.complex128)
         _load().orc_export_taylor(self._h, _ptr(e["m_row"]), _ptr(e["k_row"]), _ptr(e["skel_row"]),
                                   _ptr(e["rest_row"]), C.c_void_p(e["G_row"].ctypes.data))
+        return e
+
+
+# --------------------------------------------------------------------------
+# Section 3.3.1 and Appendix A: HSS construction (points on a line)
+# --------------------------------------------------------------------------
+
+def jacobi_rows(B):
+    """One-sided Jacobi SVD of the rows of B (m x n): (JT, sig, sweeps) with
+    B = JT^T B' for mutually orthogonal rows of B' of norms sig."""
+    B = np.array(B, dtype=np.float64, order="C")
+    m, n = B.shape
+    JT = np.empty((m, m))
+    sig = np.empty(m)
+    sw = _load().orc_jacobi_rows(_ptr(B), m, n, _ptr(JT), _ptr(sig))
+    return JT, sig, sw
+
+
+def truncated_svd_rows(A, eps_svd: float) -> np.ndarray:
+    """Left singular vectors of A (m x n) with singular values above eps_svd
+    times the largest, descending, as the rows of an s x m array (3.7)."""
+    A = np.array(A, dtype=np.float64, order="C")
+    m, n = A.shape
+    ST = np.empty((max(min(m, n), 1), m))
+    s = _load().orc_truncated_svd_rows(_ptr(A), m, n, eps_svd, _ptr(ST))
+    return ST[:s].copy()
+
+
+class HSS(H2):
+    """Oracle HSS approximation (Section 3.3.1) of A = [kappa(x_i, y_j)] for
+    points on a line: the binary tree of Section 3.1, L and L^- of (3.5),
+    the nearfield sets N_i of (A.1), the truncated SVD of each nearfield
+    block row (3.7) joined with the interpolation basis and compressed by
+    strong RRQR (3.9)/(3.13); matvec() is the Section 3.4 matvec with these
+    lists."""
+
+    def __init__(self, x, kernel: int, leaf: int, order: int, tol: float, eps_svd: float, y=None,
+                 tau: float = 0.6, f: float = 2.0):
+        lib = _load()
+        self.x = _f64(x).reshape(-1, 1)
+        self.y = None if y is None else _f64(y).reshape(-1, 1)
+        self.d = 1
+        self.kernel, self.leaf, self.order, self.tol, self.tau, self.f = kernel, leaf, order, tol, tau, f
+        self.eps_svd = eps_svd
+        ny = 0 if self.y is None else len(self.y)
+        h = lib.orc_build_hss(_ptr(self.x), len(self.x), _ptr(self.y), ny, kernel, leaf, order, tau, tol,
+                              eps_svd, f)
+        if not h:
+            raise ValueError("oracle: invalid input")
+        self._h = C.c_void_p(h)
+
+    def export(self) -> dict:
+        e = super().export()
+        nn = self.query("nnodes")
+        e["nf_ptr"] = np.empty(nn + 1, np.int64)
+        lib = _load()
+        e["nf_col"] = np.empty(max(1, self.query("nnf")), np.int32)
+        e["svd_row"] = np.empty(nn, np.int32)
+        e["svd_col"] = np.empty(nn, np.int32)
+        lib.orc_export_hss(self._h, _ptr(e["nf_ptr"]), _ptr(e["nf_col"]), _ptr(e["svd_row"]), _ptr(e["svd_col"]))
+        e["nf_col"] = e["nf_col"][: e["nf_ptr"][-1]].copy()
         return e

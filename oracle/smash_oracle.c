@@ -513,6 +513,13 @@ typedef struct orc_h2 {
     int cplx, rt;
     double cl[ORC_MAXP];
     double dx_re, dx_im;
+    /* HSS (Section 3.3.1): the nearfield sets N_i of (A.1) in CSR by node,
+     * and the number of truncated-SVD vectors s_i appended to each basis */
+    int hss;
+    double eps_svd;
+    int64_t *nf_ptr;
+    int32_t *nf_col;
+    int32_t *svd_rows, *svd_cols;
 } orc_h2;
 
 /* growable pair list */
@@ -775,6 +782,9 @@ static void orc_free_comp(orc_comp *c, int n)
 void orc_free(orc_h2 *h)
 {
     if (!h) return;
+    free(h->nf_ptr); free(h->nf_col);
+    if (h->svd_cols != h->svd_rows) free(h->svd_cols);
+    free(h->svd_rows);
     if (!h->same) { free(h->permy); free(h->keyy); free(h->ys); orc_free_comp(h->colc, h->nnodes); }
     free(h->permx); free(h->keyx); free(h->xs);
     orc_free_comp(h->rowc, h->nnodes);
@@ -968,7 +978,7 @@ int orc_matvec_abs(const orc_h2 *h, const double *q, double *z, int nrhs, const 
 enum {
     ORC_Q_NX = 0, ORC_Q_NY, ORC_Q_L, ORC_Q_NNODES, ORC_Q_NADM, ORC_Q_NNEAR, ORC_Q_SAME,
     ORC_Q_SKEL_ROW, ORC_Q_REST_ROW, ORC_Q_G_ROW, ORC_Q_SKEL_COL, ORC_Q_REST_COL, ORC_Q_G_COL,
-    ORC_Q_R, ORC_Q_SWAPS_ROW, ORC_Q_SWAPS_COL, ORC_Q_BADSWAP
+    ORC_Q_R, ORC_Q_SWAPS_ROW, ORC_Q_SWAPS_COL, ORC_Q_BADSWAP, ORC_Q_NNF
 };
 
 static void orc_comp_totals(const orc_comp *c, int n, int64_t *ts, int64_t *tr, int64_t *tg,
@@ -1007,6 +1017,7 @@ int64_t orc_query(const orc_h2 *h, int what)
     case ORC_Q_G_ROW: case ORC_Q_G_COL: return tg;
     case ORC_Q_SWAPS_ROW: case ORC_Q_SWAPS_COL: return sw;
     case ORC_Q_BADSWAP: return bad;
+    case ORC_Q_NNF: return h->nf_ptr ? h->nf_ptr[h->nnodes] : 0;
     default: return -1;
     }
 }
@@ -1592,5 +1603,316 @@ void orc_export_taylor(const orc_h2 *h, int32_t *m, int32_t *k, int64_t *skel, i
         if (ng > 0) memcpy(G + 2 * pg, c->G, sizeof(double) * 2 * (size_t)ng);
         pg += ng;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.3.1 and Appendix A: HSS construction                           */
+/* ------------------------------------------------------------------------ */
+/* The HSS tree is binary: the partition of Section 3.1 in one dimension.  The
+ * lists become (3.5): L = sibling pairs at every level, L^- = the diagonal
+ * blocks of the leaves.  Each node's basis is the interpolation basis (2.2)
+ * joined with a basis of its nearfield block row (3.7), compressed together
+ * by (3.9); the matvec of Section 3.4 then applies the HSS generators with
+ * these lists unchanged. */
+
+#define ORC_JACOBI_EPS 1e-15
+#define ORC_JACOBI_SWEEPS 60
+#define ORC_JACOBI_FLOOR 1e-30
+
+/* One-sided Jacobi SVD of the rows of B (m x n, row-major, overwritten):
+ * plane rotations of row pairs (p, q), p < q, in the round-robin order of
+ * Brent and Luk (rounds of disjoint pairs), sweep after sweep until a sweep
+ * rotates no pair (|b_p . b_q| <= eps |b_p| |b_q|) or the sweep cap.  A pair
+ * whose norm product |b_p| |b_q| is below 1e-30 of the squared Frobenius
+ * norm of the input is not rotated: with more rows than columns the surplus
+ * rows tend to zero and would otherwise keep exchanging roundoff.  JT (m x
+ * m) starts as the identity and takes the same rotations, so that the input
+ * equals JT^T B with mutually orthogonal rows of B: row p of JT is the left
+ * singular vector of the singular value sig[p] = |b_p|.  Returns the sweeps. */
+int orc_jacobi_rows(double *B, int m, int n, double *JT, double *sig)
+{
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) JT[(size_t)i * m + j] = i == j ? 1.0 : 0.0;
+    int M = m + (m & 1);
+    int sweeps = 0;
+    double frob2 = 0.0;
+    for (size_t e = 0; e < (size_t)m * n; ++e) frob2 = fma(B[e], B[e], frob2);
+    const double floor_ab = ORC_JACOBI_FLOOR * frob2;
+    for (; sweeps < ORC_JACOBI_SWEEPS && m > 1; ++sweeps) {
+        int rotated = 0;
+        for (int rr = 0; rr < M - 1; ++rr)
+            for (int i = 0; i < M / 2; ++i) {
+                int a, b;
+                if (i == 0) { a = M - 1; b = rr; }
+                else { a = (rr + i) % (M - 1); b = (rr - i + (M - 1)) % (M - 1); }
+                int p = a < b ? a : b, q = a < b ? b : a;
+                if (q >= m) continue;
+                double *bp = B + (size_t)p * n, *bq = B + (size_t)q * n;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int e = 0; e < n; ++e) {
+                    al = fma(bp[e], bp[e], al);
+                    be = fma(bq[e], bq[e], be);
+                    ga = fma(bp[e], bq[e], ga);
+                }
+                const double nab = sqrt(al) * sqrt(be);
+                if (ga == 0.0 || !(fabs(ga) > ORC_JACOBI_EPS * nab) || !(nab > floor_ab)) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double sn = c * t;
+                for (int e = 0; e < n; ++e) {
+                    double u = bp[e], v = bq[e];
+                    bp[e] = c * u - sn * v;
+                    bq[e] = sn * u + c * v;
+                }
+                double *jp = JT + (size_t)p * m, *jq = JT + (size_t)q * m;
+                for (int e = 0; e < m; ++e) {
+                    double u = jp[e], v = jq[e];
+                    jp[e] = c * u - sn * v;
+                    jq[e] = sn * u + c * v;
+                }
+                rotated = 1;
+            }
+        if (!rotated) break;
+    }
+    for (int p = 0; p < m; ++p) {
+        double s2 = 0.0;
+        for (int e = 0; e < n; ++e) s2 = fma(B[(size_t)p * n + e], B[(size_t)p * n + e], s2);
+        sig[p] = sqrt(s2);
+    }
+    return sweeps;
+}
+
+/* (3.7)/(3.11): the left singular vectors of A (m x n, destroyed) whose
+ * singular values exceed eps_svd times the largest, in descending order of
+ * the value (ties: lower index first), as the rows of ST (s x m); returns s. */
+int orc_truncated_svd_rows(double *A, int m, int n, double eps_svd, double *ST)
+{
+    if (m == 0 || n == 0) return 0;
+    double *JT = malloc(sizeof(double) * (size_t)m * m);
+    double *sig = malloc(sizeof(double) * (size_t)m);
+    int *used = calloc((size_t)m, sizeof(int));
+    orc_jacobi_rows(A, m, n, JT, sig);
+    double smax = 0.0;
+    for (int p = 0; p < m; ++p) if (sig[p] > smax) smax = sig[p];
+    int s = 0;
+    for (;;) {
+        int best = -1;
+        for (int p = 0; p < m; ++p)
+            if (!used[p] && (best < 0 || sig[p] > sig[best])) best = p;
+        if (best < 0 || !(sig[best] > eps_svd * smax) || !(sig[best] > 0.0)) break;
+        used[best] = 1;
+        memcpy(ST + (size_t)s * m, JT + (size_t)best * m, sizeof(double) * (size_t)m);
+        ++s;
+    }
+    free(JT); free(sig); free(used);
+    return s;
+}
+
+/* working set of node g on a side: leaves own their points, parents the
+ * concatenated skeletons of their children ((3.6), (3.14)) */
+static int64_t *orc_working_set(const orc_h2 *h, int g, int side, int *m_out)
+{
+    const orc_node *nd = &h->nodes[g];
+    const orc_comp *cs = side == 0 ? h->rowc : h->colc;
+    int m;
+    int64_t *ib;
+    if (nd->leaf) {
+        m = (int)(side == 0 ? nd->rc : nd->cc);
+        int64_t st = side == 0 ? nd->rs : nd->cs;
+        ib = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        for (int c = 0; c < m; ++c) ib[c] = st + c;
+    } else {
+        m = 0;
+        for (int c = 0; c < nd->nchild; ++c) m += cs[nd->child0 + c].k;
+        ib = malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        int pos = 0;
+        for (int c = 0; c < nd->nchild; ++c) {
+            const orc_comp *ch = &cs[nd->child0 + c];
+            for (int t = 0; t < ch->k; ++t) ib[pos++] = ch->skel[t];
+        }
+    }
+    *m_out = m;
+    return ib;
+}
+
+/* (3.9)/(3.13) for node g on one side: the nearfield block row (side 0:
+ * rows i_bar^row, columns j_bar^col of j in N_i) or block column (side 1,
+ * transposed), its truncated SVD, and compr of [U^_i, S_i]. */
+static void orc_compress_node_hss(orc_h2 *h, int g, int side)
+{
+    orc_node *nd = &h->nodes[g];
+    orc_comp *cp = side == 0 ? &h->rowc[g] : &h->colc[g];
+    const double *pts = side == 0 ? h->xs : h->ys;
+    const double *opts = side == 0 ? h->ys : h->xs;
+    int r = h->r, m;
+    cp->ibar = orc_working_set(h, g, side, &m);
+    cp->m = m;
+    if (m == 0) { cp->k = 0; return; }
+    /* the columns of the nearfield block: the other side's working sets of N_i */
+    int n = 0;
+    int64_t **js = malloc(sizeof(int64_t *) * (size_t)(h->nf_ptr[g + 1] - h->nf_ptr[g] + 1));
+    int *jm = malloc(sizeof(int) * (size_t)(h->nf_ptr[g + 1] - h->nf_ptr[g] + 1));
+    for (int64_t e = h->nf_ptr[g]; e < h->nf_ptr[g + 1]; ++e) {
+        js[e - h->nf_ptr[g]] = orc_working_set(h, h->nf_col[e], 1 - side, &jm[e - h->nf_ptr[g]]);
+        n += jm[e - h->nf_ptr[g]];
+    }
+    double *A = malloc(sizeof(double) * (size_t)m * (size_t)(n > 0 ? n : 1));
+    int col = 0;
+    for (int64_t e = h->nf_ptr[g]; e < h->nf_ptr[g + 1]; ++e) {
+        int64_t t = e - h->nf_ptr[g];
+        for (int b = 0; b < jm[t]; ++b, ++col)
+            for (int a = 0; a < m; ++a) {
+                const double *pa = pts + cp->ibar[a], *pb = opts + js[t][b];
+                A[(size_t)a * n + col] = side == 0 ? orc_kernel(h->kid, 1, pa, pb) : orc_kernel(h->kid, 1, pb, pa);
+            }
+        free(js[t]);
+    }
+    free(js); free(jm);
+    int smax = m < n ? m : n;
+    double *ST = malloc(sizeof(double) * (size_t)(smax > 0 ? smax : 1) * (size_t)m);
+    int s = orc_truncated_svd_rows(A, m, n, h->eps_svd, ST);
+    free(A);
+    (side == 0 ? h->svd_rows : h->svd_cols)[g] = s;
+    /* [U^_i, S_i]^T: the interpolation basis rows, then the singular vectors */
+    int rr = r + s;
+    double *Mt = malloc(sizeof(double) * (size_t)rr * (size_t)m);
+    double *P = malloc(sizeof(double) * (size_t)m);
+    for (int c = 0; c < m; ++c) P[c] = pts[cp->ibar[c]];
+    orc_basis_t(1, h->p, h->anchors, h->lo, h->s, nd->level, nd->cell, P, m, Mt);
+    memcpy(Mt + (size_t)r * m, ST, sizeof(double) * (size_t)s * m);
+    free(ST); free(P);
+    int *perm = malloc(sizeof(int) * (size_t)m);
+    int kmax = rr < m ? rr : m;
+    double *Aid = malloc(sizeof(double) * (size_t)(kmax * (m - 1) + 1));
+    int k, nsw;
+    orc_compr(Mt, rr, m, h->tol, h->f, perm, &k, Aid, &nsw);
+    cp->k = k;
+    cp->nswaps = nsw;
+    int *sel = calloc((size_t)m, sizeof(int));
+    for (int t = 0; t < k; ++t) sel[perm[t]] = 1;
+    int *rank = malloc(sizeof(int) * (size_t)m);
+    int ns = 0, nr = 0;
+    for (int pos = 0; pos < m; ++pos) rank[pos] = sel[pos] ? ns++ : nr++;
+    cp->skel = malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest = malloc(sizeof(int64_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->skel_loc = malloc(sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
+    cp->rest_loc = malloc(sizeof(int32_t) * (size_t)(m - k > 0 ? m - k : 1));
+    cp->G = malloc(sizeof(double) * (size_t)((m - k) * k > 0 ? (m - k) * k : 1));
+    for (int pos = 0; pos < m; ++pos) {
+        if (sel[pos]) { cp->skel[rank[pos]] = cp->ibar[pos]; cp->skel_loc[rank[pos]] = pos; }
+        else { cp->rest[rank[pos]] = cp->ibar[pos]; cp->rest_loc[rank[pos]] = pos; }
+    }
+    int mk = m - k;
+    for (int t = 0; t < k; ++t)
+        for (int u = 0; u < mk; ++u)
+            cp->G[(size_t)rank[perm[k + u]] * k + rank[perm[t]]] = Aid[(size_t)t * mk + u];
+    free(Mt); free(perm); free(Aid); free(sel); free(rank);
+}
+
+static int orc_i32_cmp(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    return (a > b) - (a < b);
+}
+
+/* HSS approximation (Section 3.3.1) of A = [kappa(x_i, y_j)] for points on a
+ * line (d = 1; y == NULL: Y = X), interpolation order p, separation ratio tau
+ * for the nearfield sets, SRRQR rank cut tol and bound f, truncated-SVD
+ * tolerance eps_svd of (3.8).  NULL on invalid input. */
+orc_h2 *orc_build_hss(const double *x, int64_t nx, const double *y, int64_t ny, int kid, int leaf, int p,
+                      double tau, double tol, double eps_svd, double f)
+{
+    if (nx < 1 || leaf < 1 || p < 1 || p > ORC_MAXP || !(tol > 0.0) || !(eps_svd > 0.0) ||
+        !(tau > 0.0 && tau < 1.0) || !(f > 1.0) || kid < 0 || kid > ORC_K_CAUCHY)
+        return NULL;
+    if (y && ny < 1) return NULL;
+    for (int64_t i = 0; i < nx; ++i) if (!isfinite(x[i])) return NULL;
+    if (y) for (int64_t i = 0; i < ny; ++i) if (!isfinite(y[i])) return NULL;
+    orc_h2 *h = calloc(1, sizeof(orc_h2));
+    h->d = 1; h->kid = kid; h->leaf = leaf; h->p = p; h->r = p; h->tau = tau; h->tol = tol; h->f = f;
+    h->hss = 1; h->eps_svd = eps_svd;
+    orc_chebyshev(p, h->anchors);
+    orc_structure(h, x, nx, y, ny);
+    /* (3.5): L = siblings, L^- = leaves with themselves */
+    free(h->adm_ptr); free(h->adm_col); free(h->near_ptr); free(h->near_col);
+    orc_pairs adm = {0}, near = {0};
+    for (int g = 0; g < h->nnodes; ++g) {
+        if (h->nodes[g].parent >= 0) {
+            const orc_node *pn = &h->nodes[h->nodes[g].parent];
+            for (int c = 0; c < pn->nchild; ++c)
+                if (pn->child0 + c != g) orc_pairs_push(&adm, g, pn->child0 + c);
+        }
+        if (h->nodes[g].leaf) orc_pairs_push(&near, g, g);
+    }
+    h->nadm = adm.n; h->nnear = near.n;
+    orc_to_csr(h->nnodes, &adm, &h->adm_ptr, &h->adm_col);
+    orc_to_csr(h->nnodes, &near, &h->near_ptr, &h->near_col);
+    free(adm.v); free(near.v);
+    /* (A.1), top-down: N_root empty; N_i = siblings of i, the children k of
+     * nodes of N_{p_i} with (i, k) not well separated, and the leaves of
+     * N_{p_i} not well separated from i; ascending node id */
+    h->nf_ptr = calloc((size_t)h->nnodes + 1, sizeof(int64_t));
+    int32_t **lists = calloc((size_t)h->nnodes, sizeof(int32_t *));
+    int *lcount = calloc((size_t)h->nnodes, sizeof(int));
+    for (int l = 2; l <= h->L; ++l)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            const orc_node *ni = &h->nodes[g];
+            const orc_node *pn = &h->nodes[ni->parent];
+            int cap = pn->nchild, cnt = 0;
+            for (int t = 0; t < lcount[ni->parent]; ++t) {
+                const orc_node *kq = &h->nodes[lists[ni->parent][t]];
+                cap += kq->leaf ? 1 : kq->nchild;
+            }
+            int32_t *v = malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+            for (int c = 0; c < pn->nchild; ++c)
+                if (pn->child0 + c != g) v[cnt++] = pn->child0 + c;
+            for (int t = 0; t < lcount[ni->parent]; ++t) {
+                int kq = lists[ni->parent][t];
+                const orc_node *nk = &h->nodes[kq];
+                if (nk->leaf) {
+                    if (!orc_admissible(1, ni->level, ni->cell, nk->level, nk->cell, tau)) v[cnt++] = kq;
+                } else {
+                    for (int c = 0; c < nk->nchild; ++c) {
+                        const orc_node *ch = &h->nodes[nk->child0 + c];
+                        if (!orc_admissible(1, ni->level, ni->cell, ch->level, ch->cell, tau)) v[cnt++] = nk->child0 + c;
+                    }
+                }
+            }
+            qsort(v, (size_t)cnt, sizeof(int32_t), orc_i32_cmp);
+            lists[g] = v;
+            lcount[g] = cnt;
+        }
+    for (int g = 0; g < h->nnodes; ++g) h->nf_ptr[g + 1] = h->nf_ptr[g] + lcount[g];
+    h->nf_col = malloc(sizeof(int32_t) * (size_t)(h->nf_ptr[h->nnodes] > 0 ? h->nf_ptr[h->nnodes] : 1));
+    for (int g = 0; g < h->nnodes; ++g) {
+        if (lcount[g]) memcpy(h->nf_col + h->nf_ptr[g], lists[g], sizeof(int32_t) * (size_t)lcount[g]);
+        free(lists[g]);
+    }
+    free(lists); free(lcount);
+    h->rowc = calloc((size_t)h->nnodes, sizeof(orc_comp));
+    h->colc = h->same ? h->rowc : calloc((size_t)h->nnodes, sizeof(orc_comp));
+    h->svd_rows = calloc((size_t)h->nnodes, sizeof(int32_t));
+    h->svd_cols = h->same ? h->svd_rows : calloc((size_t)h->nnodes, sizeof(int32_t));
+    /* (3.9)-(3.14): levels L..2, bottom-up; each node needs the working sets
+     * of its nearfield nodes, which are complete once the level below is */
+    for (int l = h->L; l >= 2; --l) {
+        #pragma omp parallel for schedule(dynamic)
+        for (int64_t g = h->lvl_off[l - 1]; g < h->lvl_off[l]; ++g) {
+            orc_compress_node_hss(h, (int)g, 0);
+            if (!h->same) orc_compress_node_hss(h, (int)g, 1);
+        }
+    }
+    return h;
+}
+
+/* N_i in CSR (nf_ptr: nnodes + 1, nf_col: nf_ptr[nnodes]) and the numbers
+ * of singular vectors s_i per node and side */
+void orc_export_hss(const orc_h2 *h, int64_t *nf_ptr, int32_t *nf_col, int32_t *svd_rows, int32_t *svd_cols)
+{
+    memcpy(nf_ptr, h->nf_ptr, sizeof(int64_t) * ((size_t)h->nnodes + 1));
+    if (h->nf_ptr[h->nnodes]) memcpy(nf_col, h->nf_col, sizeof(int32_t) * (size_t)h->nf_ptr[h->nnodes]);
+    memcpy(svd_rows, h->svd_rows, sizeof(int32_t) * (size_t)h->nnodes);
+    memcpy(svd_cols, h->svd_cols, sizeof(int32_t) * (size_t)h->nnodes);
 }
 
