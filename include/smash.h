@@ -64,7 +64,11 @@ enum {
      * -(1/2 pi) (y_a - x_a) / |x - y|^2, 0 at coincident points.  The double-layer
      * kernel (6.9) is sum_a of these times nu_a(y) |r'(t)| (smash_matvec_double_layer). */
     SMASH_K_DLP1 = 4,
-    SMASH_K_DLP2 = 5
+    SMASH_K_DLP2 = 5,
+    /* 1/(x - y) on the complex plane, points (x_0, x_1) read as x_0 + i x_1,
+     * complex values, d_x where the points coincide ((2.1)); only in the
+     * Taylor representation of smash_build_taylor */
+    SMASH_K_CAUCHY_C = 6
 };
 
 /* Arithmetic of the matvec (Section 3.4).  The build is always FP64. */
@@ -151,6 +155,75 @@ SMASH_API smash_status smash_build_batch(const double *points, const int64_t *of
                                          const smash_options *opt, smash_handle *out);
 
 /*
+ * smash_build_taylor -- H^2 construction of Section 3.3.2 for the kernel of
+ * (2.1) on C, kappa(x, y) = 1/(x - y) with kappa(x, x) = d_x, with the
+ * farfield basis from the Taylor expansion (2.4)-(2.5) instead of
+ * interpolation: for node i with cell centre a and radius delta (half the
+ * cell diagonal, Definition 2.1 on the cell), U^_i = [phi_{a,l}(x - a)],
+ * phi_{a,l}(t) = eta_{a,l} t^l / l!, l = 0..r-1, eta of (2.5).  compr (2.14)
+ * is the complex strong RRQR (Theorem 2.4, f = 2, Householder reflectors
+ * with real R_jj) with rank cut |R_kk| <= tol |R_11|; G is complex.  X = Y.
+ *   points  n x 2 float64 (host or device): x_0 + i x_1
+ *   r       terms of the expansion (1..64); Section 6.2 uses r = 22
+ *   tau     separation ratio of (2.3), in (0, 1); Section 6.2 uses 0.65
+ *   dx_re, dx_im  the diagonal value d_x of (2.1) (Section 6.2: 1)
+ * The tree, lists and skeleton layout are those of smash_build with dim 2;
+ * smash_export returns G_row as complex entries (two doubles each: the
+ * array must hold 2 g_row doubles).  Apply with smash_matvec_complex; the
+ * real matvec entry points reject the handle.  Synchronous.
+ * Errors: SMASH_EINVAL, SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_build_taylor(const double *points, int64_t n, int leaf_size, int r, double tau,
+                                          double tol, double dx_re, double dx_im, smash_handle *out);
+
+/*
+ * smash_matvec_complex -- Y = A^ X on a Taylor representation (Section 3.4
+ * with complex vectors, generators and kernel entries, FP64).
+ *   X, Y  n x nrhs complex, interleaved (re, im) float64, caller's point
+ *         order (2 n nrhs doubles each; host or device); Y overwritten
+ *   stream  as smash_matvec_ex
+ * Errors: SMASH_EINVAL (not a Taylor handle, NULL, nrhs outside [1, 64]),
+ * SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_matvec_complex(smash_handle h, const double *X, double *Y, int nrhs, void *stream);
+
+/*
+ * smash_build_hss -- HSS construction of Section 3.3.1 for points on a line
+ * (dim = 1, where the partition of Section 3.1 is a binary tree).
+ *   L  = the sibling pairs of every level and L^- = the leaves with
+ *        themselves (3.5);
+ *   N_i = the nearfield sets of (A.1) (siblings, children of the nodes of
+ *        N_{p_i} and leaves of N_{p_i} that are not well separated from i
+ *        with ratio opt->tau, Definition 2.1 on the cells);
+ *   for levels L..2 and each node: the nearfield block row
+ *        [A|_{i_bar^row x j_bar^col}]_{j in N_i} (3.7) and block column (3.11),
+ *        their left singular vectors above eps_svd times the largest
+ *        singular value (one-sided Jacobi), joined with the interpolation
+ *        basis (2.2) of `order` points and compressed by strong RRQR (3.9),
+ *        (3.13); rank cut |R_kk| <= tol |R_11|, f = opt->f.
+ *   B_i and D_i of (3.15) are kept as index sets and evaluated on the fly.
+ * Arguments as smash_build_xy with dim = 1 (y == NULL: Y = X); kernel_id in
+ * 0..3.  At most 64 singular vectors per node (SMASH_ENOTSUP above that).
+ * Apply with smash_matvec / smash_matvec_ex in every precision except
+ * SMASH_PREC_F32X2 (its digit scaling needs well-separated pairs).
+ * Synchronous.  Errors: SMASH_EINVAL, SMASH_ENOMEM, SMASH_ECUDA, SMASH_ENOTSUP.
+ */
+SMASH_API smash_status smash_build_hss(const double *x, int64_t nx, const double *y, int64_t ny, int kernel_id,
+                                       int leaf_size, int order, double tol, double eps_svd,
+                                       const smash_options *opt, smash_handle *out);
+
+/*
+ * smash_export_hss -- the nearfield sets N_i of an HSS representation in
+ * CSR by global node id (nf_ptr: nnodes + 1 entries; nf_col: *nnf entries,
+ * written only if cap >= *nnf) and the number of singular vectors appended
+ * to each node's row and column basis (svd_row, svd_col: nnodes entries).
+ * Host memory; NULL skips an array; *nnf is always written.
+ * Errors: SMASH_EINVAL (not an HSS handle), SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_export_hss(smash_handle h, int64_t *nf_ptr, int32_t *nf_col, int64_t cap,
+                                        int32_t *svd_row, int32_t *svd_col, int64_t *nnf);
+
+/*
  * smash_matvec -- Y = A^ X by the node-wise algorithm of Section 3.4:
  * upward pass (q^_i = V_i^T q, then W_c^T), coupling over L with kernel
  * blocks on skeleton pairs, downward pass (R_c, then U_i), near field over L^-.
@@ -235,14 +308,19 @@ SMASH_API smash_status smash_matvec_cauchy_like(smash_handle h, const double *w,
  * holds until the process exits; problems whose scratch does not fit, i.e.
  * 8 * ldq * (nx + ny + skeleton slots of rows and columns) bytes beyond that
  * maximum (ldq = nrhs rounded up to a power of two, or to a multiple of 32
- * above 32), are rejected with SMASH_EINVAL and a message.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  The
- * handle's device must be the current device.  Every call overwrites each
- * scratch region before reading it, so no state carries over between calls,
- * but all calls share the one array: calls whose GPU work overlaps (on
- * different streams, or from different threads) race and must be ordered by
- * the caller.  Errors: SMASH_EINVAL, SMASH_ECUDA.
+ * above 32), are rejected with SMASH_EINVAL and a message.  The array is
+ * committed on a device by the first build on it (smash_build*, which looks
+ * up its device address with cudaGetSymbolAddress with that device current),
+ * so a caller that builds before handing the remaining device memory to its
+ * own allocator finds the array already in place; if that lookup failed, the
+ * first smash_matvec_noalloc call on the device repeats it (make that call
+ * before any stream capture).  The handle's device must be the current
+ * device.  Every call overwrites each scratch region before reading it, so
+ * no state carries over between calls, but all calls share the one array:
+ * calls whose GPU work overlaps race and must be ordered by the caller.  That
+ * includes the default: stream == NULL means each handle's own stream, so
+ * NULL-stream calls on two different handles run on two streams and race;
+ * pass one stream to all of them.  Errors: SMASH_EINVAL, SMASH_ECUDA.
  */
 #define SMASH_NOALLOC_SCRATCH_BYTES (64u << 20)
 SMASH_API smash_status smash_matvec_noalloc(smash_handle h, const double *X, double *Y, int nrhs, void *stream);
@@ -383,6 +461,20 @@ typedef struct {
 
 SMASH_API smash_status smash_export(smash_handle h, const smash_export_t *out);
 
+/*
+ * smash_near_fallback_leaves -- the leaves whose near-field rows (3.20) the
+ * SMASH_PREC_F32X2 matvec does not take through the digit-split products but
+ * through its double-float kernel: a row of the leaf meets a source at the
+ * same coordinates (other than its own point), or its sources span more than
+ * 2^12 in distance, so a per-row digit exponent would lose accuracy.  The
+ * classification depends on the points only.  Writes up to cap global node
+ * ids (ascending) to leaves (host memory) and the total to *count; *count = 0
+ * when the handle's matvec has no digit-split near field (kernels other than
+ * 1/|x-y| and 1/(x-y)).  Synchronous (runs the classification on the
+ * handle's stream).  Errors: SMASH_EINVAL, SMASH_ENOMEM, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_near_fallback_leaves(smash_handle h, int32_t *leaves, int64_t cap, int64_t *count);
+
 /* Device bytes held by a handle (0 for NULL). */
 SMASH_API size_t smash_footprint_bytes(smash_handle h);
 
@@ -417,6 +509,16 @@ SMASH_API smash_status smash_autotune_save(const char *path);
 SMASH_API int smash_autotune_entries(void);
 SMASH_API void smash_autotune_clear(void);
 SMASH_API int smash_autotune_lookup(const char *key, int *value);
+
+/*
+ * smash_measure_fma_peak -- measured arithmetic peak of the current device in
+ * TFLOP/s: a launch of independent fused multiply-add chains over every SM
+ * (fp64 != 0: FP64, else FP32), best of three CUDA-event-timed runs, 2 flops
+ * per FMA.  The paper has no counterpart: it is the denominator of the
+ * roofline fractions this library reports for its ALU-bound kernels.
+ * Synchronous, ~0.2 s.  Errors: SMASH_EINVAL, SMASH_ECUDA.
+ */
+SMASH_API smash_status smash_measure_fma_peak(int fp64, double *tflops);
 
 /* Message of the last failed call on this host thread ("" if none). */
 SMASH_API const char *smash_last_error(void);

@@ -24,7 +24,9 @@ __all__ = [
     "smash_matvec_graph", "smash_matvec_graph_count", "smash_matvec_cauchy_like", "smash_matvec_kernel",
     "smash_matvec_double_layer", "SMASH_K_DLP1", "SMASH_K_DLP2", "smash_set_autotune", "smash_autotune_load",
     "smash_autotune_save", "smash_autotune_entries", "smash_autotune_clear", "smash_autotune_lookup",
-    "smash_matvec_noalloc", "smash_free",
+    "smash_matvec_noalloc", "smash_near_fallback_leaves", "smash_build_taylor", "smash_matvec_complex",
+    "smash_build_hss", "smash_export_hss",
+    "SMASH_K_CAUCHY_C", "smash_measure_fma_peak", "smash_node_ranks", "smash_free",
     "smash_info", "smash_export", "smash_footprint_bytes", "smash_predict_footprint",
     "smash_suggest_rank", "smash_last_error", "smash_launch_count", "smash_set_profiling",
     "smash_last_profile", "H2Matrix", "SmashServer", "load_library", "library_path",
@@ -35,6 +37,7 @@ __all__ = [
 
 SMASH_K_LOG, SMASH_K_INVR, SMASH_K_YUKAWA, SMASH_K_CAUCHY1D = 0, 1, 2, 3
 SMASH_K_DLP1, SMASH_K_DLP2 = 4, 5
+SMASH_K_CAUCHY_C = 6
 SMASH_PREC_F64 = 0
 SMASH_PREC_F32X2 = 1
 SMASH_PREC_F32 = 2
@@ -106,6 +109,14 @@ def load_library(build: bool = True):
     lib.smash_build_xy.restype = i32
     lib.smash_build_batch.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, C.POINTER(P)]
     lib.smash_build_batch.restype = i32
+    lib.smash_build_taylor.argtypes = [P, i64, i32, i32, dbl, dbl, dbl, dbl, C.POINTER(P)]
+    lib.smash_build_taylor.restype = i32
+    lib.smash_matvec_complex.argtypes = [P, P, P, i32, P]
+    lib.smash_matvec_complex.restype = i32
+    lib.smash_build_hss.argtypes = [P, i64, P, i64, i32, i32, i32, dbl, dbl, P, C.POINTER(P)]
+    lib.smash_build_hss.restype = i32
+    lib.smash_export_hss.argtypes = [P, P, P, i64, P, P, C.POINTER(i64)]
+    lib.smash_export_hss.restype = i32
     lib.smash_matvec_kernel.argtypes = [P, i32, P, P, i32, i32, P]
     lib.smash_matvec_kernel.restype = i32
     lib.smash_matvec_double_layer.argtypes = [P, P, P, P, P, P, i32, i32, P]
@@ -140,6 +151,10 @@ def load_library(build: bool = True):
     lib.smash_info.restype = i32
     lib.smash_export.argtypes = [P, P]
     lib.smash_export.restype = i32
+    lib.smash_near_fallback_leaves.argtypes = [P, P, i64, C.POINTER(i64)]
+    lib.smash_near_fallback_leaves.restype = i32
+    lib.smash_measure_fma_peak.argtypes = [i32, C.POINTER(dbl)]
+    lib.smash_measure_fma_peak.restype = i32
     lib.smash_footprint_bytes.argtypes = [P]
     lib.smash_footprint_bytes.restype = C.c_size_t
     lib.smash_predict_footprint.argtypes = [i64, i32, i32, i32, i32]
@@ -195,6 +210,19 @@ def _rows(a) -> int:
     return int(a.shape[0])
 
 
+def _check_shapes(h, X, Y, nrhs: int):
+    """X must be ny x nrhs and Y nx x nrhs: the C ABI takes bare pointers and
+    cannot check sizes, so an undersized buffer would be read or written out
+    of bounds."""
+    i = smash_info(h)
+    for name, a, rows in (("X", X, i["ny"]), ("Y", Y, i["nx"])):
+        shape = tuple(int(v) for v in a.shape)
+        if len(shape) != 2 or shape[0] != rows or shape[1] < nrhs:
+            raise ValueError(f"{name} must have shape ({rows}, {nrhs}), got {shape}")
+        if shape[1] != nrhs:
+            raise ValueError(f"{name} must have exactly nrhs = {nrhs} columns (rows are packed), got {shape}")
+
+
 def _check(st: int):
     if st != 0:
         raise SmashError(st, load_library(False).smash_last_error().decode())
@@ -243,9 +271,79 @@ def smash_build_batch(points, offsets, kernel_id: int, leaf_size: int, order: in
     return h
 
 
+def smash_build_taylor(points, leaf_size: int, r: int, tau: float = 0.65, tol: float = 1e-14,
+                       dx: complex = 1.0 + 0.0j):
+    """smash_build_taylor: the Taylor representation (2.4) of 1/(x - y) on C
+    for n x 2 float64 points (x_0 + i x_1); see smash.h."""
+    lib = load_library()
+    h = C.c_void_p()
+    dx = complex(dx)
+    _check(lib.smash_build_taylor(_ptr(points), int(points.shape[0]), leaf_size, r, float(tau), float(tol),
+                                  dx.real, dx.imag, C.byref(h)))
+    return h
+
+
+def _cptr(a):
+    """Data pointer of a complex128 torch tensor or numpy array (interleaved)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.complex128":
+            raise ValueError("expected a contiguous complex128 tensor")
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.complex128:
+            raise ValueError("expected a C-contiguous complex128 array")
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def smash_matvec_complex(h, X, Y, stream=None):
+    """Y = A^ X on a Taylor representation; X, Y n x nrhs complex128."""
+    lib = load_library()
+    i = smash_info(h)
+    nrhs = int(X.shape[1])
+    for name, a in (("X", X), ("Y", Y)):
+        if tuple(int(v) for v in a.shape) != (i["nx"], nrhs):
+            raise ValueError(f"{name} must have shape ({i['nx']}, {nrhs}), got {tuple(a.shape)}")
+    _check(lib.smash_matvec_complex(h, _cptr(X), _cptr(Y), nrhs, _stream_ptr(stream)))
+    return Y
+
+
+def smash_build_hss(x, y, kernel_id: int, leaf_size: int, order: int, tol: float, eps_svd: float,
+                    tau: float = 0.6, f: float = 2.0, stream=None):
+    """smash_build_hss: the HSS representation (Section 3.3.1) for points on
+    a line (x: n x 1, y: m x 1 or None); see smash.h."""
+    lib = load_library()
+    for name, a in (("x", x), ("y", y)):
+        if a is not None and (len(a.shape) != 2 or int(a.shape[1]) != 1):
+            raise ValueError(f"{name} must be n x 1 (points on a line), got {tuple(a.shape)}")
+    h = C.c_void_p()
+    opt = smash_options(tau, f, _stream_ptr(stream))
+    nx = int(x.shape[0])
+    ny = 0 if y is None else int(y.shape[0])
+    _check(lib.smash_build_hss(_ptr(x), nx, _ptr(y), ny, kernel_id, leaf_size, order, float(tol), float(eps_svd),
+                               C.byref(opt), C.byref(h)))
+    return h
+
+
+def smash_export_hss(h) -> dict:
+    """N_i (CSR by node) and the singular vectors per node of an HSS handle."""
+    lib = load_library()
+    nn = smash_info(h)["nnodes"]
+    nnf = C.c_int64(0)
+    _check(lib.smash_export_hss(h, None, None, 0, None, None, C.byref(nnf)))
+    out = {"nf_ptr": np.empty(nn + 1, np.int64), "nf_col": np.empty(max(nnf.value, 1), np.int32),
+           "svd_row": np.empty(nn, np.int32), "svd_col": np.empty(nn, np.int32)}
+    _check(lib.smash_export_hss(h, C.c_void_p(out["nf_ptr"].ctypes.data), C.c_void_p(out["nf_col"].ctypes.data),
+                                len(out["nf_col"]), C.c_void_p(out["svd_row"].ctypes.data),
+                                C.c_void_p(out["svd_col"].ctypes.data), C.byref(nnf)))
+    out["nf_col"] = out["nf_col"][: nnf.value].copy()
+    return out
+
+
 def smash_matvec(h, X, Y, nrhs: int | None = None):
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check_shapes(h, X, Y, nrhs)
     _check(lib.smash_matvec(h, _ptr(X), _ptr(Y), nrhs))
     return Y
 
@@ -253,6 +351,7 @@ def smash_matvec(h, X, Y, nrhs: int | None = None):
 def smash_matvec_ex(h, X, Y, precision: int = SMASH_PREC_F64, stream=None, nrhs: int | None = None):
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check_shapes(h, X, Y, nrhs)
     _check(lib.smash_matvec_ex(h, _ptr(X), _ptr(Y), nrhs, precision, _stream_ptr(stream)))
     return Y
 
@@ -261,6 +360,7 @@ def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
     """Y = A^ X without device allocation (X, Y device tensors); see smash.h."""
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check_shapes(h, X, Y, nrhs)
     _check(lib.smash_matvec_noalloc(h, _ptr(X), _ptr(Y), nrhs, _stream_ptr(stream)))
     return Y
 
@@ -268,6 +368,7 @@ def smash_matvec_noalloc(h, X, Y, stream=None, nrhs: int | None = None):
 def smash_matvec_kernel(h, kernel_id: int, X, Y, precision: int = SMASH_PREC_F64, stream=None):
     """Y = A^_kappa X with another kernel on the same representation (see smash.h)."""
     lib = load_library()
+    _check_shapes(h, X, Y, int(X.shape[1]))
     _check(lib.smash_matvec_kernel(h, kernel_id, _ptr(X), _ptr(Y), int(X.shape[1]), precision, _stream_ptr(stream)))
     return Y
 
@@ -293,6 +394,7 @@ def smash_matvec_graph(h, X, Y, precision: int = SMASH_PREC_F64, stream=None, nr
     """Y = A^ X replayed from a CUDA graph captured at the first call (device X, Y)."""
     lib = load_library()
     nrhs = int(X.shape[1]) if nrhs is None else nrhs
+    _check_shapes(h, X, Y, nrhs)
     _check(lib.smash_matvec_graph(h, _ptr(X), _ptr(Y), nrhs, precision, _stream_ptr(stream)))
     return Y
 
@@ -364,7 +466,8 @@ def smash_export(h) -> dict:
         arrs[f"k_{tag}"] = np.empty(nn, np.int32)
         arrs[f"skel_{tag}"] = np.empty(i[f"skel_{tag}"], np.int64)
         arrs[f"rest_{tag}"] = np.empty(i[f"rest_{tag}"], np.int64)
-        arrs[f"G_{tag}"] = np.empty(i[f"g_{tag}"], np.float64)
+        # a Taylor representation (kernel 6) has complex G
+        arrs[f"G_{tag}"] = np.empty(i[f"g_{tag}"], np.complex128 if i["kernel_id"] == SMASH_K_CAUCHY_C else np.float64)
     ex = smash_export_t(*[C.c_void_p(arrs[name].ctypes.data) if arrs[name].size else None
                           for name in _EXPORT_FIELDS])
     _check(lib.smash_export(h, C.byref(ex)))
@@ -372,6 +475,38 @@ def smash_export(h) -> dict:
     arrs["lo"] = np.array(i["lo"][: i["dim"]])
     arrs["s"] = i["s"]
     return arrs
+
+
+def smash_near_fallback_leaves(h) -> np.ndarray:
+    """Global ids of the leaves the double-float matvec's digit-split near
+    field leaves to its double-float kernel (see smash.h)."""
+    lib = load_library()
+    cnt = C.c_int64(0)
+    _check(lib.smash_near_fallback_leaves(h, None, 0, C.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), np.int32)
+    _check(lib.smash_near_fallback_leaves(h, C.c_void_p(out.ctypes.data), len(out), C.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def smash_measure_fma_peak(fp64: bool) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (FP64 or FP32)."""
+    v = C.c_double(0.0)
+    _check(load_library().smash_measure_fma_peak(1 if fp64 else 0, C.byref(v)))
+    return float(v.value)
+
+
+def smash_node_ranks(h, side: str = "row") -> dict:
+    """Per node: level, leaf flag, working-set size m and rank k (one side),
+    through smash_export with every other array skipped."""
+    lib = load_library()
+    i = smash_info(h)
+    nn = i["nnodes"]
+    arrs = {"level": np.empty(nn, np.int32), "leaf": np.empty(nn, np.int32),
+            f"m_{side}": np.empty(nn, np.int32), f"k_{side}": np.empty(nn, np.int32)}
+    ex = smash_export_t(*[C.c_void_p(arrs[name].ctypes.data) if name in arrs and nn else None
+                          for name in _EXPORT_FIELDS])
+    _check(lib.smash_export(h, C.byref(ex)))
+    return {"level": arrs["level"], "leaf": arrs["leaf"], "m": arrs[f"m_{side}"], "k": arrs[f"k_{side}"]}
 
 
 def smash_footprint_bytes(h) -> int:

@@ -138,8 +138,10 @@ static void export_side(const smash_h2 *h, const Side &S, bool rows, int32_t *m_
     auto start = fetch(rows ? h->rs : h->cs, nn, s);
     auto loc = fetch(S.loc, S.total_loc, s);
     auto skg = fetch(S.skel_gidx, S.total_skel, s);
+    // a Taylor representation's G is complex: two doubles per entry
+    const int gw = h->taylor ? 2 : 1;
     std::vector<double> G;
-    if (G_out) G = fetch(S.G, S.total_g, s);
+    if (G_out) G = fetch(S.G, S.total_g * gw, s);
     CK(cudaStreamSynchronize(s));
     int64_t ps = 0, pr = 0, pg = 0;
     for (int64_t g = 0; g < nn; ++g) {
@@ -152,7 +154,7 @@ static void export_side(const smash_h2 *h, const Side &S, bool rows, int32_t *m_
         for (int u = 0; u < mk; ++u, ++pr)
             if (rest_out) rest_out[pr] = gid(loc[loc_off[g] + kk + u]);
         int64_t ng = (int64_t)mk * kk;
-        if (G_out) std::memcpy(G_out + pg, G.data() + g_off[g], ng * sizeof(double));
+        if (G_out) std::memcpy(G_out + gw * pg, G.data() + gw * g_off[g], gw * ng * sizeof(double));
         pg += ng;
     }
 }
@@ -177,9 +179,18 @@ smash_status smash_build(const double *points, int dim, int64_t n, int kernel_id
 // Shared by smash_build_xy and smash_build_batch: offsets == nullptr builds
 // one problem (x, y); otherwise x holds nproblems independent problems with
 // X = Y each, problem t owning rows [offsets[t], offsets[t+1]).
+struct TaylorSpec {
+    double dx_re, dx_im;
+};
+
+struct HssSpec {
+    double eps_svd;
+};
+
 static smash_status build_impl(const double *x, int64_t nx, const double *y, int64_t ny, const int64_t *offsets,
                                int nproblems, int dim, int kernel_id, int leaf_size, int order, double tol,
-                               const smash_options *opt, smash_handle *out) {
+                               const smash_options *opt, smash_handle *out, const TaylorSpec *taylor = nullptr,
+                               const HssSpec *hss = nullptr) {
     if (out) *out = nullptr;
     smash_h2 *h = nullptr;
     try {
@@ -195,9 +206,20 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
         if (order < 1 || order > kMaxP) fail(SMASH_EINVAL, "order must be in [1, %d]", kMaxP);
         int r = 1;
         for (int a = 0; a < dim; ++a) r *= order;
+        if (taylor) r = order;  // r terms of the expansion (2.4)
         if (r > kMaxR) fail(SMASH_EINVAL, "order^dim = %d exceeds %d", r, kMaxR);
         if (!(tol > 0.0) || !std::isfinite(tol)) fail(SMASH_EINVAL, "tol must be positive and finite");
-        check_kernel(kernel_id, dim);
+        if (taylor) {
+            if (dim != 2 || y || offsets) fail(SMASH_EINVAL, "the Taylor representation takes one 2D point set");
+            if (!std::isfinite(taylor->dx_re) || !std::isfinite(taylor->dx_im)) fail(SMASH_EINVAL, "d_x must be finite");
+        } else {
+            check_kernel(kernel_id, dim);
+        }
+        if (hss) {
+            if (dim != 1 || offsets) fail(SMASH_EINVAL, "the HSS construction takes one point set on a line (dim 1)");
+            if (kernel_id > SMASH_K_CAUCHY1D) fail(SMASH_EINVAL, "the HSS construction supports kernels 0..3");
+            if (!(hss->eps_svd > 0.0) || !std::isfinite(hss->eps_svd)) fail(SMASH_EINVAL, "eps_svd must be positive");
+        }
         if (!(o.tau > 0.0 && o.tau < 1.0)) fail(SMASH_EINVAL, "tau must be in (0, 1)");
         if (!(o.f > 1.0)) fail(SMASH_EINVAL, "f must be > 1");
 
@@ -212,9 +234,23 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
         h->nx = nx; h->ny = y ? ny : nx;
         h->bits = bits_per_dim(dim);
         chebyshev(order, h->anchors);
+        if (hss) {
+            h->hss = 1;
+            h->eps_svd = hss->eps_svd;
+        }
+        if (taylor) {
+            // the node-independent factors of (2.5): eta_{v,l} = (cl[l] / delta_v)^l
+            const double pi = 3.14159265358979323846;
+            h->taylor = 1;
+            h->dx_re = taylor->dx_re;
+            h->dx_im = taylor->dx_im;
+            const double rho = pow(2.0 * pi * (double)r, 1.0 / (2.0 * (double)r));
+            for (int l = 0; l < r; ++l) h->taylor_cl[l] = ((double)l / exp(1.0)) * rho;
+        }
         CK(cudaGetDevice(&h->device));
         CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
         init_pool_once(h->device);
+        noalloc_prepare(h->device);
         if (o.stream) {
             h->stream = (cudaStream_t)o.stream;
         } else {
@@ -242,9 +278,11 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
         tm.mark();
         build_tree(h, scratch);
         tm.mark();
-        build_lists(h, scratch);
+        if (h->hss) build_lists_hss(h, scratch);
+        else build_lists(h, scratch);
         tm.mark();
-        build_compression(h, scratch);
+        if (h->hss) build_compression_hss(h, scratch);
+        else build_compression(h, scratch);
         {
             // normalised two-float copies of the point and skeleton coordinates for
             // the SMASH_PREC_F32X2 and SMASH_PREC_F32 matvecs
@@ -263,8 +301,9 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
                 dd_coords(h->colside.skel_xyz, h->colside.total_skel, h->lo, h->s, h->colside.skel_dd, h->stream);
             }
         }
-        if (dd_supported(h->kernel_id)) {
-            // exact three-float copies: points (near field) and, for deep trees, skeletons
+        {
+            // exact three-float copies of the points: the near field of the
+            // double-float matvec, and the close pairs of the FP32 near field
             h->dd_e = dd_exact_exponent(h->s);
             h->xs_x3 = h->mem.alloc<float>((size_t)h->nx * 12);
             dd_coords3(h->xs, h->nx, h->dd_e, h->xs_x3, h->stream);
@@ -274,6 +313,9 @@ static smash_status build_impl(const double *x, int64_t nx, const double *y, int
                 h->ys_x3 = h->mem.alloc<float>((size_t)h->ny * 12);
                 dd_coords3(h->ys, h->ny, h->dd_e, h->ys_x3, h->stream);
             }
+        }
+        if (dd_supported(h->kernel_id)) {
+            // and, for deep trees, of the skeletons
             if (dd_exact_coupling(h)) {
                 h->row.skel_x3 = h->mem.alloc<float>((size_t)std::max<int64_t>(h->row.total_skel, 1) * 12);
                 dd_coords3(h->row.skel_xyz, h->row.total_skel, h->dd_e, h->row.skel_x3, h->stream);
@@ -307,6 +349,75 @@ extern "C" {
 smash_status smash_build_xy(const double *x, int64_t nx, const double *y, int64_t ny, int dim, int kernel_id,
                             int leaf_size, int order, double tol, const smash_options *opt, smash_handle *out) {
     return build_impl(x, nx, y, ny, nullptr, 1, dim, kernel_id, leaf_size, order, tol, opt, out);
+}
+
+smash_status smash_build_taylor(const double *points, int64_t n, int leaf_size, int r, double tau, double tol,
+                                double dx_re, double dx_im, smash_handle *out) {
+    smash_options o;
+    smash_default_options(&o);
+    o.tau = tau;
+    TaylorSpec spec{dx_re, dx_im};
+    return build_impl(points, n, nullptr, 0, nullptr, 1, 2, SMASH_K_CAUCHY_C, leaf_size, r, tol, &o, out, &spec);
+}
+
+smash_status smash_build_hss(const double *x, int64_t nx, const double *y, int64_t ny, int kernel_id, int leaf_size,
+                             int order, double tol, double eps_svd, const smash_options *opt, smash_handle *out) {
+    smash_options o;
+    smash_default_options(&o);
+    if (opt) o = *opt;
+    HssSpec spec{eps_svd};
+    return build_impl(x, nx, y, ny, nullptr, 1, 1, kernel_id, leaf_size, order, tol, &o, out, nullptr, &spec);
+}
+
+smash_status smash_export_hss(smash_handle h, int64_t *nf_ptr, int32_t *nf_col, int64_t cap, int32_t *svd_row,
+                              int32_t *svd_col, int64_t *nnf) {
+    try {
+        if (!h || !nnf) fail(SMASH_EINVAL, "NULL argument");
+        if (!h->hss) fail(SMASH_EINVAL, "not an HSS representation");
+        *nnf = h->nnf;
+        cudaStream_t s = h->stream;
+        CK(cudaStreamSynchronize(s));
+        if (nf_ptr) CK(cudaMemcpy(nf_ptr, h->nf_ptr, sizeof(int64_t) * (h->nnodes + 1), cudaMemcpyDeviceToHost));
+        if (nf_col && cap >= h->nnf && h->nnf > 0)
+            CK(cudaMemcpy(nf_col, h->nf_col, sizeof(int32_t) * h->nnf, cudaMemcpyDeviceToHost));
+        if (svd_row) CK(cudaMemcpy(svd_row, h->svd_row, sizeof(int32_t) * h->nnodes, cudaMemcpyDeviceToHost));
+        if (svd_col) CK(cudaMemcpy(svd_col, h->svd_col, sizeof(int32_t) * h->nnodes, cudaMemcpyDeviceToHost));
+        return SMASH_OK;
+    } catch (const Error &e) {
+        return record(e);
+    }
+}
+
+smash_status smash_matvec_complex(smash_handle h, const double *X, double *Y, int nrhs, void *stream) {
+    try {
+        if (!h) fail(SMASH_EINVAL, "handle is NULL");
+        if (!h->taylor) fail(SMASH_EINVAL, "smash_matvec_complex needs a handle from smash_build_taylor");
+        if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
+        if (nrhs < 1 || nrhs > kMaxNrhs) fail(SMASH_EINVAL, "nrhs must be in [1, %d]", kMaxNrhs);
+        cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+        Arena io(s);
+        const size_t bytes = sizeof(double) * 2 * (size_t)h->nx * nrhs;
+        const double *Xd = X;
+        double *Yd = Y;
+        const bool yhost = !is_device_ptr(Y);
+        if (!is_device_ptr(X)) {
+            double *t = io.alloc<double>(2 * (size_t)h->nx * nrhs);
+            CK(cudaMemcpyAsync(t, X, bytes, cudaMemcpyHostToDevice, s));
+            Xd = t;
+        }
+        if (yhost) Yd = io.alloc<double>(2 * (size_t)h->nx * nrhs);
+        h->prof_mv.on = profiling_enabled();
+        matvec_taylor(h, Xd, Yd, nrhs, s, &h->prof_mv);
+        if (yhost) CK(cudaMemcpyAsync(Y, Yd, bytes, cudaMemcpyDeviceToHost, s));
+        io.release();
+        if (yhost || !stream) CK(cudaStreamSynchronize(s));
+        return SMASH_OK;
+    } catch (const Error &e) {
+        return record(e);
+    } catch (const std::bad_alloc &) {
+        t_last_error = "host allocation failed";
+        return SMASH_ENOMEM;
+    }
 }
 
 smash_status smash_build_batch(const double *points, const int64_t *offsets, int nproblems, int dim, int kernel_id,
@@ -344,6 +455,7 @@ void check_kernel(int kernel_id, int dim) {
 
 void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int nrhs, int precision, int kid) {
     if (!h) fail(SMASH_EINVAL, "handle is NULL");
+    if (h->taylor) fail(SMASH_EINVAL, "a Taylor representation is complex: use smash_matvec_complex");
     if (kid < 0) kid = h->kernel_id;
     check_kernel(kid, h->dim);
     if (!X || !Y) fail(SMASH_EINVAL, "X or Y is NULL");
@@ -352,8 +464,12 @@ void check_matvec_args(const smash_h2 *h, const double *X, const double *Y, int 
         fail(SMASH_EINVAL, "unknown precision %d", precision);
     if (precision == SMASH_PREC_F32X2 && !dd_supported(kid))
         fail(SMASH_EINVAL, "SMASH_PREC_F32X2 supports the kernels 1/|x-y| and 1/(x-y) only");
-    if (precision == SMASH_PREC_F32X2 && !h->xs_x3)
+    if (precision == SMASH_PREC_F32X2 && !dd_supported(h->kernel_id))
         fail(SMASH_EINVAL, "SMASH_PREC_F32X2 needs a handle built for 1/|x-y| or 1/(x-y)");
+    // the digit-split kernel sums scale entries by bounds that hold for
+    // well-separated pairs; HSS sibling pairs need not be
+    if (precision == SMASH_PREC_F32X2 && h->hss)
+        fail(SMASH_EINVAL, "SMASH_PREC_F32X2 is not available on an HSS representation");
 }
 
 void run_matvec(const smash_h2 *h, const double *X, double *Y, int nrhs, int precision, cudaStream_t s,

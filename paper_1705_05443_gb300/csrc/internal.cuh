@@ -157,6 +157,21 @@ struct smash_h2 {
     // statistics
     int64_t swaps = 0, swap_cap_hits = 0, coupling_pairs = 0, near_pairs = 0;
     int64_t rest_row = 0, g_row = 0, rest_col = 0, g_col = 0;  // exact sums of m-k and (m-k)k
+    // the Taylor-expansion representation of 1/(x - y) on C (smash_build_taylor):
+    // complex G and vectors, r = order terms, cl[l] = (l/e)(2 pi r)^(1/(2r)),
+    // kappa(x, x) = d_x
+    int taylor = 0;
+    double taylor_cl[smash::kMaxP] = {0};
+    double dx_re = 0.0, dx_im = 0.0;
+    // the HSS representation (smash_build_hss, d = 1): L and L^- of (3.5), the
+    // nearfield sets N_i of (A.1) in CSR, the truncated-SVD tolerance of (3.8)
+    // and the singular vectors appended to each node's basis (rows, columns)
+    int hss = 0;
+    double eps_svd = 0.0;
+    int64_t nnf = 0;
+    int64_t *nf_ptr = nullptr;
+    int32_t *nf_col = nullptr;
+    int32_t *svd_row = nullptr, *svd_col = nullptr;
     smash::Profile prof_build, prof_mv;
     smash::GraphCache *graphs = nullptr;  // captured matvecs (smash_matvec_graph)
 };
@@ -168,6 +183,8 @@ void build_geometry(smash_h2 *h, const double *x_dev, const double *y_dev, Arena
 void build_geometry_batch(smash_h2 *h, const double *x_dev, Arena &scratch);
 void build_tree(smash_h2 *h, Arena &scratch);
 void build_lists(smash_h2 *h, Arena &scratch);
+void build_lists_hss(smash_h2 *h, Arena &scratch);
+void build_compression_hss(smash_h2 *h, Arena &scratch);
 void build_compression(smash_h2 *h, Arena &scratch);
 void build_stats(smash_h2 *h, Arena &scratch);
 
@@ -219,6 +236,13 @@ void matvec_scatter(const smash_h2 *h, const double *zs, int ldq, int nrhs, doub
 size_t matvec_f64_scratch_bytes(const smash_h2 *h, int nrhs);
 void matvec_f64_scratch(const smash_h2 *h, const double *X_dev, double *Y_dev, int nrhs, cudaStream_t s,
                         void *scratch, size_t scratch_bytes);
+// The complex matvec of a Taylor representation (X, Y: nx x nrhs complex,
+// interleaved, device memory).
+void matvec_taylor(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStream_t s, Profile *prof);
+
+// Commits the static scratch of smash_matvec_noalloc on device dev (the
+// current device); called by every build.
+void noalloc_prepare(int dev);
 
 bool profiling_enabled();
 

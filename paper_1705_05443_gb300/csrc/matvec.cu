@@ -422,6 +422,9 @@ void matvec_f64_scratch(const smash_h2 *h, const double *X, double *Y, int nrhs,
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs; a.ys = h->ys; a.qv = qs; a.out = zs; a.ldq = ldq;
+        // nullptr handle: the untuned default shape of each kernel sum, so that
+        // this path never times candidates (tuning allocates); it can be slower
+        // than the shape smash_matvec_ex picks with tuning on
         ksum(nullptr, h->kernel_id, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     for (int l = h->L; l >= 2; --l) {

@@ -4,7 +4,13 @@
 //  * Differences come from the normalised two-float coordinates
 //    x'' = 1 + (x - lo)/s in [1, 2): (hi_a - hi_b) is exact (Sterbenz) and
 //    (lo_a - lo_b) restores the low bits, so a difference is accurate to
-//    ~2^-48 in absolute terms before it is rounded to FP32.
+//    ~2^-47 in absolute terms before it is rounded to FP32.  That is below
+//    half an FP32 ulp of the difference for pairs at least 2^-22 apart (in
+//    units of the cube side).  The near field meets closer pairs too (the
+//    interlaced points of Section 6.3 lie 1e-7 U(0,1) apart): for a pair
+//    closer than 2^-22 it recomputes the difference from the exact
+//    three-float coordinates with an error-free sum, so every entry keeps
+//    FP32 accuracy.
 //  * The kernel entry, the products and the sums are FP32 (relative error of
 //    an entry ~1e-7).  The coupling accumulates in FP32; the near field, whose
 //    closest pairs dominate their rows, accumulates with Kahan's compensated
@@ -32,6 +38,9 @@ struct KsumF32Args {
     const int32_t *s_cnt;
     const float *xt;   // normalised two-float coordinates, 8 floats per point
     const float *ys;
+    const float *xt3;  // exact three-float coordinates x 2^-e, 12 floats per point (near field)
+    const float *ys3;
+    float x3_norm;     // 2^e / s: a difference in the three-float frame times this is normalised
     const float *qv;   // source vectors, FP32, ldq per point
     double *out;       // target vectors (FP64), ldq
     double scale;      // multiplies the sums (1/s for 1/r and 1/(x-y), else 1)
@@ -44,6 +53,29 @@ struct KsumF32Args {
 
 constexpr int kF32Threads = 256;
 constexpr int kF32Tile = 256;
+
+// x - y, normalised, from the exact three-float coordinates of a close pair:
+// the hi parts differ exactly (Sterbenz), the mid parts by an error-free
+// TwoSum, the lo parts (below 2^-48 of the coordinate) by a rounded
+// difference; the parts are then added from the smallest up and rounded once
+// more by the normalisation.
+template <int D>
+__device__ __forceinline__ void exact_diff3(const float *x3, const float *y3, float norm, float *d) {
+    const float4 xh = reinterpret_cast<const float4 *>(x3)[0], xm = reinterpret_cast<const float4 *>(x3)[1],
+                 xl = reinterpret_cast<const float4 *>(x3)[2];
+    const float4 yh = reinterpret_cast<const float4 *>(y3)[0], ym = reinterpret_cast<const float4 *>(y3)[1],
+                 yl = reinterpret_cast<const float4 *>(y3)[2];
+    const float h[3] = {xh.x - yh.x, xh.y - yh.y, xh.z - yh.z};
+    const float am[3] = {xm.x, xm.y, xm.z}, bm[3] = {-ym.x, -ym.y, -ym.z};
+    const float l[3] = {xl.x - yl.x, xl.y - yl.y, xl.z - yl.z};
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const float sm = am[c] + bm[c];
+        const float bb = sm - am[c];
+        const float err = (am[c] - (sm - bb)) + (bm[c] - bb);
+        d[c] = ((h[c] + sm) + (err + l[c])) * norm;
+    }
+}
 
 // One thread: TA targets x RC right-hand sides; the right-hand sides of a
 // source are read from shared memory as float4 (RC >= 4) and reused by the
@@ -125,6 +157,14 @@ __global__ void __launch_bounds__(kF32Threads, (KAHAN && RC >= 32) || (!KAHAN &&
                     for (int u = 0; u < TA; ++u) {
                         float d[3] = {(xh[u].x - yh.x) + (xl[u].x - yl.x), (xh[u].y - yh.y) + (xl[u].y - yl.y),
                                       (xh[u].z - yh.z) + (xl[u].z - yl.z)};
+                        if (KAHAN && have[u]) {
+                            float r2 = d[0] * d[0];
+                            if (D > 1) r2 = fmaf(d[1], d[1], r2);
+                            if (D > 2) r2 = fmaf(d[2], d[2], r2);
+                            if (r2 < 0x1p-44f)
+                                exact_diff3<D>(a.xt3 + (toff + tb + ta + u * tbp) * 12, a.ys3 + sidx[b] * 12,
+                                               a.x3_norm, d);
+                        }
                         kv[u] = have[u] ? kappa_f32<KID, D>(d, a.s_f, a.inv_s, a.log_s) : 0.f;
                     }
                     const float *qb = sq + (size_t)b * ldq + ch * RC;
@@ -294,6 +334,7 @@ void matvec_f32(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStr
         a.tnodes = h->leaf_list; a.t_off = h->rs; a.t_cnt = h->rc;
         a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
         a.xt = h->xs_dd; a.ys = h->ys_dd; a.qv = qs1; a.out = zs; a.ldq = ldq;
+        a.xt3 = h->xs_x3; a.ys3 = h->ys_x3; a.x3_norm = (float)(ldexp(1.0, h->dd_e) / h->s);
         ksum_f32(h, kid, true, a, h->nleaves, std::min<int64_t>(h->leaf_size, 256), RC, s);
     }
     tm.mark();

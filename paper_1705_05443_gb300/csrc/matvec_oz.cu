@@ -48,6 +48,8 @@
 #include <cuda_bf16.h>
 
 #include "dd_arith.cuh"
+#include <vector>
+
 #include "internal.cuh"
 #include "ksum_tiles.cuh"
 
@@ -797,3 +799,42 @@ void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, 
 }
 
 }  // namespace smash
+
+using namespace smash;
+
+// Leaves that the digit-split near field leaves to the double-float kernel:
+// the classification of near_oz run on zero right-hand sides (it depends on
+// the points only), flags copied back and mapped to global node ids.
+extern "C" smash_status smash_near_fallback_leaves(smash_handle h, int32_t *leaves, int64_t cap, int64_t *count) {
+    try {
+        if (!h || !count) fail(SMASH_EINVAL, "NULL argument");
+        if (cap < 0 || (cap > 0 && !leaves)) fail(SMASH_EINVAL, "leaves must hold cap entries");
+        *count = 0;
+        const int ldq = 8;
+        if (!near_oz_supported(h, h->kernel_id, ldq)) return SMASH_OK;
+        cudaStream_t s = h->stream;
+        Arena tmp(s);
+        double *qs = tmp.alloc<double>((size_t)h->ny * ldq);
+        double *zs = tmp.alloc<double>((size_t)h->nx * ldq);
+        int *fb = tmp.alloc<int>((size_t)std::max<int64_t>(h->nleaves, 1));
+        CK(cudaMemsetAsync(qs, 0, sizeof(double) * (size_t)h->ny * ldq, s));
+        CK(cudaMemsetAsync(zs, 0, sizeof(double) * (size_t)h->nx * ldq, s));
+        near_oz(h, h->kernel_id, qs, zs, ldq, fb, s);
+        std::vector<int> flags((size_t)h->nleaves);
+        std::vector<int32_t> ids((size_t)h->nleaves);
+        CK(cudaMemcpyAsync(flags.data(), fb, sizeof(int) * (size_t)h->nleaves, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ids.data(), h->leaf_list, sizeof(int32_t) * (size_t)h->nleaves, cudaMemcpyDeviceToHost,
+                           s));
+        CK(cudaStreamSynchronize(s));
+        tmp.release();
+        for (int64_t i = 0; i < h->nleaves; ++i) {
+            if (!flags[(size_t)i]) continue;
+            if (*count < cap) leaves[*count] = ids[(size_t)i];
+            ++*count;
+        }
+        return SMASH_OK;
+    } catch (const Error &e) {
+        set_last_error(e.msg.c_str());
+        return e.status;
+    }
+}

@@ -40,6 +40,25 @@ void *scratch_address(int dev) {
     return g_addr[dev];
 }
 
+}  // namespace
+
+// Looks the scratch up on device dev (the current device) so that the module
+// holding it is loaded and its 64 MiB committed now.  The CUDA runtime loads a
+// module lazily, at its first use; without this the first
+// smash_matvec_noalloc call would be the one to commit the array, possibly
+// after a caller's own pool allocator has taken the free memory.  The build
+// calls this once per device; a failure here is left for that first
+// smash_matvec_noalloc call to report.
+void noalloc_prepare(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    try {
+        scratch_address(dev);
+    } catch (const Error &) {
+    }
+}
+
+namespace {
+
 bool on_device(const void *p) {
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);

@@ -662,4 +662,143 @@ void build_lists(smash_h2 *h, Arena &scratch) {
     scratch.free(near);
 }
 
+// ------------------------------------------------------------------ HSS lists
+// (3.5): L = the siblings of every node, L^- = every leaf with itself.
+__global__ void hss_count_kernel(int64_t nn, const int32_t *__restrict__ parent, const int32_t *__restrict__ nchild,
+                                 const int32_t *__restrict__ leaf, int32_t *__restrict__ ca,
+                                 int32_t *__restrict__ cn) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nn) return;
+    ca[g] = parent[g] >= 0 ? nchild[parent[g]] - 1 : 0;
+    cn[g] = leaf[g] ? 1 : 0;
+}
+
+__global__ void hss_fill_kernel(int64_t nn, const int32_t *__restrict__ parent, const int32_t *__restrict__ child0,
+                                const int32_t *__restrict__ nchild, const int32_t *__restrict__ leaf,
+                                const int64_t *__restrict__ adm_ptr, int32_t *__restrict__ adm_col,
+                                const int64_t *__restrict__ near_ptr, int32_t *__restrict__ near_col) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nn) return;
+    const int32_t p = parent[g];
+    if (p >= 0) {
+        int64_t o = adm_ptr[g];
+        for (int c = 0; c < nchild[p]; ++c)
+            if (child0[p] + c != g) adm_col[o++] = child0[p] + c;
+    }
+    if (leaf[g]) near_col[near_ptr[g]] = (int32_t)g;
+}
+
+// (A.1) for the nodes of one level: N_i = the siblings of i, the children k of
+// the non-leaf nodes of N_{p_i} with (i, k) not well separated, and the leaves
+// of N_{p_i} not well separated from i; ascending node id.  Two passes: count,
+// then fill and sort.
+__device__ __forceinline__ int nf_visit(NodeArrays A, int d, double tau, int64_t g, const int64_t *__restrict__ nf_ptr,
+                                        const int32_t *__restrict__ nf_col, int32_t *out) {
+    const int32_t p = A.parent[g];
+    int cnt = 0;
+    for (int c = 0; c < A.nchild[p]; ++c) {
+        const int32_t k = A.child0[p] + c;
+        if (k == g) continue;
+        if (out) out[cnt] = k;
+        ++cnt;
+    }
+    for (int64_t e = nf_ptr[p]; e < nf_ptr[p + 1]; ++e) {
+        const int32_t kq = nf_col[e];
+        if (A.leaf[kq]) {
+            if (!admissible(d, A.level[g], A.cell + 3 * g, A.level[kq], A.cell + 3 * (int64_t)kq, tau)) {
+                if (out) out[cnt] = kq;
+                ++cnt;
+            }
+        } else {
+            for (int c = 0; c < A.nchild[kq]; ++c) {
+                const int32_t k = A.child0[kq] + c;
+                if (!admissible(d, A.level[g], A.cell + 3 * g, A.level[k], A.cell + 3 * (int64_t)k, tau)) {
+                    if (out) out[cnt] = k;
+                    ++cnt;
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
+__global__ void nf_count_kernel(NodeArrays A, int d, double tau, int64_t n0, int64_t nl,
+                                const int64_t *__restrict__ nf_ptr, const int32_t *__restrict__ nf_col,
+                                int32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    cnt[i] = nf_visit(A, d, tau, n0 + i, nf_ptr, nf_col, nullptr);
+}
+
+__global__ void nf_fill_kernel(NodeArrays A, int d, double tau, int64_t n0, int64_t nl, const int64_t *__restrict__ nf_ptr,
+                               int32_t *__restrict__ nf_col) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    const int64_t g = n0 + i;
+    int32_t *out = nf_col + nf_ptr[g];
+    const int cnt = nf_visit(A, d, tau, g, nf_ptr, nf_col, out);
+    for (int a = 1; a < cnt; ++a) {  // insertion sort: the lists hold a handful of nodes
+        int32_t v = out[a];
+        int b = a - 1;
+        while (b >= 0 && out[b] > v) { out[b + 1] = out[b]; --b; }
+        out[b + 1] = v;
+    }
+}
+
+void build_lists_hss(smash_h2 *h, Arena &scratch) {
+    cudaStream_t s = h->stream;
+    const int64_t nn = h->nnodes;
+    const unsigned blocks = (unsigned)((nn + 255) / 256);
+    int32_t *ca = scratch.alloc<int32_t>(nn), *cn = scratch.alloc<int32_t>(nn);
+    int64_t *tot = scratch.alloc<int64_t>(3);
+    hss_count_kernel<<<blocks, 256, 0, s>>>(nn, h->parent, h->nchild, h->leaf, ca, cn);
+    LAUNCHED();
+    h->adm_ptr = h->mem.alloc<int64_t>(nn + 1);
+    h->near_ptr = h->mem.alloc<int64_t>(nn + 1);
+    exclusive_scan<int32_t>(ca, h->adm_ptr, nn, nullptr, h->adm_ptr + nn, s, scratch);
+    exclusive_scan<int32_t>(cn, h->near_ptr, nn, nullptr, h->near_ptr + nn, s, scratch);
+    int64_t ht[2];
+    CK(cudaMemcpyAsync(&ht[0], h->adm_ptr + nn, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&ht[1], h->near_ptr + nn, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->nadm = ht[0];
+    h->nnear = ht[1];
+    h->adm_col = h->mem.alloc<int32_t>(std::max<int64_t>(h->nadm, 1));
+    h->near_col = h->mem.alloc<int32_t>(std::max<int64_t>(h->nnear, 1));
+    hss_fill_kernel<<<blocks, 256, 0, s>>>(nn, h->parent, h->child0, h->nchild, h->leaf, h->adm_ptr, h->adm_col,
+                                           h->near_ptr, h->near_col);
+    LAUNCHED();
+    // the nearfield sets, level by level from the top
+    NodeArrays A{h->level, h->leaf, h->parent, h->child0, h->nchild, h->rc, h->cc, h->rs, h->cs, h->cell,
+                 h->node_tree};
+    h->nf_ptr = h->mem.alloc<int64_t>(nn + 1);
+    CK(cudaMemsetAsync(h->nf_ptr, 0, sizeof(int64_t) * (nn + 1), s));
+    int64_t cap = std::max<int64_t>(nn, 16), used = 0;
+    h->nf_col = h->mem.alloc<int32_t>(cap);
+    CK(cudaMemsetAsync(tot, 0, 8, s));
+    for (int l = 2; l <= h->L; ++l) {
+        const int64_t n0 = h->lvl_off[l - 1], nl = h->lvl_off[l] - n0;
+        const unsigned lb = (unsigned)((nl + 255) / 256);
+        nf_count_kernel<<<lb, 256, 0, s>>>(A, h->dim, h->tau, n0, nl, h->nf_ptr, h->nf_col, ca);
+        LAUNCHED();
+        exclusive_scan<int32_t>(ca, h->nf_ptr + n0, nl, tot, tot, s, scratch);
+        // the end of the level's last list (the next level's scan writes the same value)
+        CK(cudaMemcpyAsync(h->nf_ptr + n0 + nl, tot, 8, cudaMemcpyDeviceToDevice, s));
+        int64_t total = 0;
+        CK(cudaMemcpyAsync(&total, tot, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (total > cap) {
+            const int64_t c2 = std::max(2 * cap, total);
+            grow(h->nf_col, used, c2, h->mem, s);
+            cap = c2;
+        }
+        nf_fill_kernel<<<lb, 256, 0, s>>>(A, h->dim, h->tau, n0, nl, h->nf_ptr, h->nf_col);
+        LAUNCHED();
+        used = total;
+    }
+    h->nnf = used;
+    CK(cudaStreamSynchronize(s));
+    scratch.free(ca); scratch.free(cn); scratch.free(tot);
+}
+
 }  // namespace smash

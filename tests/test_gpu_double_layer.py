@@ -2,8 +2,10 @@
 on the GPU.
 
 Parity: K X by smash_matvec_double_layer against the oracle's H^2 matvecs of
-the two gradient kernels (6.9) combined in numpy, at the bars of the matvec
-precisions (FP64 1e-11; FP32 and split TF32 1e-5).  Physics: with sigma = 1
+the two gradient kernels (6.9) combined in numpy, entry by entry at the bars
+of the matvec precisions against each entry's sum of |terms| (parity_helpers:
+FP64 1e-12; FP32 and split TF32 1e-5; relative 2-norm 1e-11 / 1e-5 as a
+second line).  Physics: with sigma = 1
 the discretised double layer on the curve is -1/2 (Gauss), to the H^2
 approximation error.  The representation is kernel-independent: applying a
 kernel by override equals a handle built for that kernel, bit for bit.
@@ -13,6 +15,7 @@ import pytest
 
 import oracle
 import smash_inputs as si
+from parity_helpers import TOL_F32, TOL_F64, TOL_TF32X3, assert_entrywise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,21 +49,28 @@ def curve(request):
 
 
 def _oracle_double_layer(c, X):
+    """K X from the oracle's H^2 matvecs of the two gradient kernels, and each
+    entry's sum of |terms|."""
     nu, w = c["nu"], c["w"]
     z = np.zeros_like(X)
+    sc = np.zeros_like(X)
     for a, kid in ((0, 4), (1, 5)):
         ho = oracle.H2(c["x"], kid, LEAF, ORDER, TOL)
-        z += ho.matvec(np.ascontiguousarray((nu[:, a] * w)[:, None] * X))
-    return z + c["diag"][:, None] * X
+        qa = np.ascontiguousarray((nu[:, a] * w)[:, None] * X)
+        z += ho.matvec(qa)
+        sc += ho.matvec_abs(qa)
+    return z + c["diag"][:, None] * X, sc + np.abs(c["diag"][:, None] * X)
 
 
 def test_double_layer_parity_with_the_oracle(curve):
     X = si.rhs(len(curve["x"]), 3, 7100)
-    zo = _oracle_double_layer(curve, X)
-    for prec, bar in ((sm.SMASH_PREC_F64, 1e-11), (sm.SMASH_PREC_F32, 1e-5), (sm.SMASH_PREC_TF32X3, 1e-5)):
+    zo, sc = _oracle_double_layer(curve, X)
+    for prec, bar, ebar in ((sm.SMASH_PREC_F64, 1e-11, TOL_F64), (sm.SMASH_PREC_F32, 1e-5, TOL_F32),
+                            (sm.SMASH_PREC_TF32X3, 1e-5, TOL_TF32X3)):
         Y = torch.empty_like(_dev(X))
         sm.smash_matvec_double_layer(curve["h"].h, _dev(curve["nu"]), _dev(curve["w"]), _dev(curve["diag"]),
                                      _dev(X), Y, prec)
+        assert_entrywise(Y.cpu().numpy(), zo, sc, ebar, what=f"precision {prec}")
         assert _rel(Y.cpu().numpy(), zo) <= bar, prec
 
 

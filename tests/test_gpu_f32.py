@@ -6,13 +6,18 @@ within a few ulps (~2e-7 relative; differences are taken from two-float
 coordinates, so close pairs lose nothing before the rounding to FP32), the
 products and the coupling sums are FP32 (errors of random sign: ~1e-7 times
 the row's scale), the near field is Kahan-compensated, the transfers are FP64.
-Observed errors are ~1e-7..1e-6, one to two orders inside the bar.
+Observed errors are ~1e-7..1e-6, one to two orders inside the bar.  Every
+comparison with the oracle is entry by entry: each difference within 1e-5 of
+the entry's sum of |terms| (parity_helpers); the relative 2-norm is a second
+line.
 """
 import numpy as np
 import pytest
 
 import oracle
 import smash_inputs as si
+from parity_helpers import (TOL_BF16, TOL_F32, TOL_F64, TOL_TF32, TOL_TF32X3, assert_entrywise, leaf_rows,
+                            oracle_reference, sample_leaves)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -48,9 +53,10 @@ CASES = [
 def test_f32_matches_oracle(name, xf, yf, kid, leaf, order, tol, nrhs):
     x = xf()
     q = si.rhs(len(x), nrhs, 404)
-    zo = oracle.H2(x, kid, leaf, order, tol).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, kid, leaf, order, tol), q)
     H = sm.H2Matrix(_dev(x), kid, leaf, order, tol)
     z = H.matvec(_dev(q), precision=F32).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32, what=name)
     err = _rel(z, zo)
     assert err <= RTOL, f"{name}: {err:.3e}"
     H.close()
@@ -59,27 +65,38 @@ def test_f32_matches_oracle(name, xf, yf, kid, leaf, order, tol, nrhs):
 def test_f32_cauchy_rectangular():
     x, y = si.cauchy_1d(6000, 405)
     q = si.rhs(6000, 4, 406)
-    zo = oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y), q)
     H = sm.H2Matrix(_dev(x), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=_dev(y))
     z = H.matvec(_dev(q), precision=F32).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32, what="cauchy x != y")
     assert _rel(z, zo) <= RTOL
     H.close()
 
 
-def test_f32_sphere_yukawa_full_size():
+def test_sphere_yukawa_full_size_against_the_oracle(sphere_oracle):
     """The mixed-precision workload at N = 2^20 (sphere with caps, Yukawa,
-    order 5, 32 RHS): FP32 against the FP64 matvec of the same handle on all
-    rows (the FP64 path is bit-exact to the oracle's build and within 1e-11 of
-    its matvec), and against the dense product on sampled rows."""
-    w = si.make_workload("sphere_yukawa_1m")
+    order 5, 32 RHS): every precision against the FP64 oracle entry by entry
+    on the rows of 64 sampled leaves (about 4100 rows: box corners, face
+    centres, the rest at random), against the FP64 GPU matvec on all rows,
+    and the FP64 result against the dense product on sampled rows."""
+    w, ho, eo = sphere_oracle
     x, q = w["x"], w["q"]
     H = sm.H2Matrix(_dev(x), w["kernel"], w["leaf"], w["order"], w["tol"])
     qd = _dev(q)
-    z32 = H.matvec(qd, precision=F32).cpu().numpy()
     z64 = H.matvec(qd).cpu().numpy()
-    assert _rel(z32, z64) <= RTOL
-    rows = si.sample_rows(len(x), 128, 407)
-    zd = oracle.dense_rows(x, w["kernel"], q, rows=rows)
-    err = _rel(z64[rows], zd)
+    pick = sample_leaves(eo, x, 64, seed=4)
+    rows = leaf_rows(eo, pick)
+    assert len(rows) >= 3000
+    zo, sc = oracle_reference(ho, q, pick)
+    assert_entrywise(z64, zo, sc, TOL_F64, rows=rows, what="f64")
+    for p, etol, rtol in ((F32, TOL_F32, RTOL), (sm.SMASH_PREC_TF32X3, TOL_TF32X3, 1e-5),
+                          (sm.SMASH_PREC_TF32, TOL_TF32, 1e-3), (sm.SMASH_PREC_BF16, TOL_BF16, 8e-3)):
+        z = H.matvec(qd, precision=p).cpu().numpy()
+        assert_entrywise(z, zo, sc, etol, rows=rows, what=f"precision {p}")
+        assert _rel(z[rows], zo[rows]) <= rtol, p
+        assert _rel(z, z64) <= rtol, p
+    sel = si.sample_rows(len(x), 128, 407)
+    zd = oracle.dense_rows(x, w["kernel"], q, rows=sel)
+    err = _rel(z64[sel], zd)
     assert err < 1e-3, err
     H.close()

@@ -7,13 +7,16 @@ FP64 path.  Error budget: coordinates carry ~2^-48 relative precision in the
 unit-cube frame (~1e-13 relative in a difference at leaf distances), the
 reciprocal square root one Newton step from a 2-ulp seed (< 3e-14), products
 and sums are error-free up to the renormalisation of the accumulators once per
-128 sources (~1e-13 over the longest rows).
+128 sources (~1e-13 over the longest rows).  Compared entry by entry: each
+difference within 1e-11 of the entry's sum of |terms| (parity_helpers); the
+relative 2-norm stays a second line at 1e-11.
 """
 import numpy as np
 import pytest
 
 import oracle
 import smash_inputs as si
+from parity_helpers import TOL_F32X2, assert_entrywise, leaf_rows, oracle_reference, sample_leaves
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,9 +44,10 @@ def _rel(a, b):
 def test_invr_f32x2_matches_oracle(d, n, leaf, order, nrhs):
     x = si.uniform_cube(n, d, 300 + d)
     q = si.rhs(n, nrhs, 301)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, leaf, order, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, leaf, order, 1e-8), q)
     H = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, leaf, order, 1e-8)
     z = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32X2, what=f"d={d} nrhs={nrhs}")
     assert _rel(z, zo) <= RTOL
     H.close()
 
@@ -51,9 +55,10 @@ def test_invr_f32x2_matches_oracle(d, n, leaf, order, nrhs):
 def test_clustered_sphere_f32x2_matches_oracle():
     x = si.sphere_with_caps(12000, 310)
     q = si.rhs(12000, 8, 311)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     H = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     z = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32X2, what="sphere")
     assert _rel(z, zo) <= RTOL
     H.close()
 
@@ -61,9 +66,10 @@ def test_clustered_sphere_f32x2_matches_oracle():
 def test_cauchy_rectangular_f32x2_matches_oracle():
     x, y = si.cauchy_1d(6000, 320)
     q = si.rhs(6000, 4, 321)
-    zo = oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y), q)
     H = sm.H2Matrix(_dev(x), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=_dev(y))
     z = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32X2, what="cauchy x != y")
     assert _rel(z, zo) <= RTOL
     H.close()
 
@@ -77,21 +83,41 @@ def test_unsupported_kernel_is_rejected():
     H.close()
 
 
-def test_full_size_headline_workload_f32x2():
-    """N = 2^20: the double-float matvec on the points of sampled leaves
-    against the oracle's H^2 matvec on the same leaves, and against the
-    library's FP64 matvec on all rows."""
-    w = si.make_workload("3d_invr_1m")
+def test_full_size_headline_workload_f32x2(headline_oracle):
+    """N = 2^20: the double-float matvec entry by entry on the rows of 64
+    sampled leaves (box corners and faces, every leaf the digit-split near
+    field leaves to its fallback, the rest at random) against the oracle's
+    H^2 matvec on the same leaves, and against the library's FP64 matvec on
+    all rows."""
+    w, ho, eo = headline_oracle
     x, q = w["x"], w["q"]
     H = sm.H2Matrix(_dev(x), w["kernel"], w["leaf"], w["order"], w["tol"])
     z2 = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
     z64 = H.matvec(_dev(q)).cpu().numpy()
     assert _rel(z2, z64) <= RTOL
-    ho = oracle.H2(x, w["kernel"], w["leaf"], w["order"], w["tol"])
+    fb = sm.smash_near_fallback_leaves(H.h)
+    pick = sample_leaves(eo, x, 64, seed=2, extra=fb)
+    assert len(pick) >= 64 and set(fb.tolist()) <= set(pick.tolist())
+    zo, sc = oracle_reference(ho, q, pick)
+    rows = leaf_rows(eo, pick)
+    assert_entrywise(z2, zo, sc, TOL_F32X2, rows=rows, what="N=2^20 sampled leaves")
+    H.close()
+
+
+def test_full_size_with_coincident_points_f32x2():
+    """N = 2^18 with 200 points duplicated: the leaves holding them are left
+    by the digit-split near field to the double-float kernel; all of them,
+    and random others, are compared entry by entry with the oracle."""
+    x = si.uniform_cube(1 << 18, 3, 340)
+    x = np.concatenate([x, x[:200]])
+    q = si.rhs(len(x), 16, 341)
+    ho = oracle.H2(x, sm.SMASH_K_INVR, 128, 4, 1e-8)
     eo = ho.export()
-    leaves = np.flatnonzero(eo["leaf"])
-    pick = leaves[np.linspace(0, len(leaves) - 1, 4).astype(int)].astype(np.int32)
-    zo = ho.matvec_leaves(q, pick)
-    rows = np.concatenate([eo["permx"][eo["rs"][g]:eo["rs"][g] + eo["rc"][g]] for g in pick])
-    assert _rel(z2[rows], zo[rows]) <= RTOL
+    H = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 128, 4, 1e-8)
+    z = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    fb = sm.smash_near_fallback_leaves(H.h)
+    assert len(fb) > 0, "coincident points must take the fallback"
+    pick = sample_leaves(eo, x, len(fb) + 32, seed=3, extra=fb)
+    zo, sc = oracle_reference(ho, q, pick)
+    assert_entrywise(z, zo, sc, TOL_F32X2, rows=leaf_rows(eo, pick), what="fallback leaves")
     H.close()

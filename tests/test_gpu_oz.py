@@ -8,8 +8,9 @@ from 8 columns per pass, else the second):
      combined in double-float;
   1. every operation in double-float on the FP32 pipe.
 Both carry ~2^-46 relative precision per entry, so both meet the FP64 bar
-(1e-11 relative 2-norm against the oracle's FP64 H^2 matvec) and agree with
-each other far below it.  Blocks the digit split does not cover (more than
+(entry by entry within 1e-11 of each entry's sum of |terms| against the
+oracle's FP64 H^2 matvec, parity_helpers; relative 2-norm 1e-11 as a second
+line) and agree with each other far below it.  Blocks the digit split does not cover (more than
 16 right-hand sides per pass; trees on the exact three-float coordinates)
 take the second way.
 """
@@ -20,6 +21,7 @@ import pytest
 
 import oracle
 import smash_inputs as si
+from parity_helpers import TOL_F32X2, assert_entrywise, oracle_reference
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -75,13 +77,15 @@ def _forced(h, q, table, keys, path, choice):
 def test_both_couplings_match_the_oracle(clean_table, tmp_path, d, n, leaf, order, nrhs):
     x = si.uniform_cube(n, d, 6100 + d)
     q = si.rhs(n, nrhs, 6101)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, leaf, order, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, leaf, order, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, leaf, order, 1e-8)
     table, keys, path = _coupling_keys(h, q, tmp_path)
     assert keys, "the digit-split coupling is offered for this tree"
     z0 = _forced(h, q, table, keys, path, 0)
     z1 = _forced(h, q, table, keys, path, 1)
+    assert_entrywise(z0, zo, sc, TOL_F32X2)
     assert _rel(z0, zo) <= RTOL
+    assert_entrywise(z1, zo, sc, TOL_F32X2)
     assert _rel(z1, zo) <= RTOL
     # the two ways differ only by roundings of the double-float arithmetic
     assert _rel(z0, z1) <= 1e-12
@@ -93,11 +97,12 @@ def test_default_matvec_takes_the_digit_split_coupling(clean_table):
     is deterministic (fixed reduction order) and meets the bar."""
     x = si.sphere_with_caps(12000, 6200)
     q = si.rhs(12000, 16, 6201)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     za = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
     zb = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
     assert np.array_equal(za, zb)
+    assert_entrywise(za, zo, sc, TOL_F32X2)
     assert _rel(za, zo) <= RTOL
     h.close()
 
@@ -105,12 +110,14 @@ def test_default_matvec_takes_the_digit_split_coupling(clean_table):
 def test_cauchy_rectangular_digit_split(clean_table, tmp_path):
     x, y = si.cauchy_1d(6000, 6300)
     q = si.rhs(6000, 4, 6301)
-    zo = oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=y), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=_dev(y))
     table, keys, path = _coupling_keys(h, q, tmp_path)
     assert keys
     for choice in (0, 1):
-        assert _rel(_forced(h, q, table, keys, path, choice), zo) <= RTOL, choice
+        z = _forced(h, q, table, keys, path, choice)
+        assert_entrywise(z, zo, sc, TOL_F32X2, what=f"choice {choice}")
+        assert _rel(z, zo) <= RTOL, choice
     h.close()
 
 
@@ -121,7 +128,7 @@ def test_wide_scales_of_q_columns(clean_table, tmp_path):
     q = si.rhs(10000, 8, 6401)
     q = q * (2.0 ** np.array([-40, -13, 0, 7, 19, 40, 0, 3]))[None, :]
     q[:, 6] = 0.0
-    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     table, keys, path = _coupling_keys(h, q, tmp_path)
     z = _forced(h, q, table, keys, path, 0)
@@ -129,6 +136,7 @@ def test_wide_scales_of_q_columns(clean_table, tmp_path):
         if c == 6:
             assert not np.any(z[:, c])
         else:
+            assert_entrywise(z[:, c], zo[:, c], sc[:, c], TOL_F32X2, what=f"column {c}")
             assert _rel(z[:, c], zo[:, c]) <= RTOL, c
     h.close()
 
@@ -140,11 +148,13 @@ def test_wide_blocks_take_the_double_float_coupling(clean_table, tmp_path, nrhs)
     the bar."""
     x = si.uniform_cube(8000, 3, 6500)
     q = si.rhs(8000, nrhs, 6501)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     _, keys, _ = _coupling_keys(h, q, tmp_path)
     assert not keys
-    assert _rel(h.matvec(_dev(q), precision=F32X2).cpu().numpy(), zo) <= RTOL
+    z = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    assert_entrywise(z, zo, sc, TOL_F32X2, what=f"nrhs={nrhs}")
+    assert _rel(z, zo) <= RTOL
     h.close()
 
 
@@ -178,13 +188,15 @@ def test_both_near_fields_match_the_oracle(clean_table, tmp_path, case):
         (x, y), kern, leaf, order, tol = si.cauchy_1d(6000, 6604), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10
     n = len(x) if y is None else len(y)
     q = si.rhs(n, 16, 6605)
-    zo = oracle.H2(x, kern, leaf, order, tol, y=y).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, kern, leaf, order, tol, y=y), q)
     h = sm.H2Matrix(_dev(x), kern, leaf, order, tol, y=None if y is None else _dev(y))
     table, keys, path = _near_keys(h, q, tmp_path)
     assert keys, "the digit-split near field is offered"
     z0 = _forced(h, q, table, keys, path, 0)
     z1 = _forced(h, q, table, keys, path, 1)
+    assert_entrywise(z0, zo, sc, TOL_F32X2)
     assert _rel(z0, zo) <= RTOL
+    assert_entrywise(z1, zo, sc, TOL_F32X2)
     assert _rel(z1, zo) <= RTOL
     assert _rel(z0, z1) <= 1e-12
     h.close()
@@ -197,11 +209,12 @@ def test_coincident_points_take_the_double_float_near_field(clean_table, tmp_pat
     x = si.uniform_cube(8000, 3, 6700)
     x = np.concatenate([x, x[:300]])  # 300 coincident pairs
     q = si.rhs(len(x), 16, 6701)
-    zo = oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8).matvec(q)
+    zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     table, keys, path = _near_keys(h, q, tmp_path)
     assert keys
     z0 = _forced(h, q, table, keys, path, 0)
     assert np.all(np.isfinite(z0))
+    assert_entrywise(z0, zo, sc, TOL_F32X2)
     assert _rel(z0, zo) <= RTOL
     h.close()

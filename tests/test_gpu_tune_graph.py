@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import smash_inputs as si
+from parity_helpers import TOL_F32, TOL_F32X2, TOL_F64, TOL_TF32, assert_entrywise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,7 +51,7 @@ def test_tuned_build_and_matvec_keep_parity(clean_table, tmp_path):
     q = si.rhs(30000, 16, 4101)
     ho = oracle.H2(x, 1, 128, 4, 1e-8)
     eo = ho.export()
-    zo = ho.matvec(q)
+    zo, sc = ho.matvec(q), ho.matvec_abs(q)
     sm.smash_set_autotune(True)
     h = sm.H2Matrix(_dev(x), 1, 128, 4, 1e-8)
     z = {p: h.matvec(_dev(q), precision=p).cpu().numpy()
@@ -59,7 +60,9 @@ def test_tuned_build_and_matvec_keep_parity(clean_table, tmp_path):
     assert sm.smash_autotune_entries() >= 4
     e1 = h.export()
     _same(e1, eo)
-    for p, tol in ((sm.SMASH_PREC_F64, 1e-11), (sm.SMASH_PREC_F32X2, 1e-11), (sm.SMASH_PREC_F32, 1e-5)):
+    for p, tol, etol in ((sm.SMASH_PREC_F64, 1e-11, TOL_F64), (sm.SMASH_PREC_F32X2, 1e-11, TOL_F32X2),
+                         (sm.SMASH_PREC_F32, 1e-5, TOL_F32)):
+        assert_entrywise(z[p], zo, sc, etol, what=f"tuned precision {p}")
         assert np.linalg.norm(z[p] - zo) / np.linalg.norm(zo) <= tol, p
     path = tmp_path / "tune.json"
     sm.smash_autotune_save(str(path))
@@ -157,7 +160,7 @@ def test_tcgen05_coupling_candidate_keeps_the_tf32_bar(clean_table, tmp_path):
     x = si.sphere_with_caps(10000, 4500)
     q = si.rhs(10000, 32, 4501)
     ho = oracle.H2(x, 2, 128, 5, 1e-8)
-    zo = ho.matvec(q)
+    zo, sc = ho.matvec(q), ho.matvec_abs(q)
     sm.smash_set_autotune(True)
     h = sm.H2Matrix(_dev(x), 2, 128, 5, 1e-8)
     h.matvec(_dev(q), precision=sm.SMASH_PREC_TF32)
@@ -174,5 +177,6 @@ def test_tcgen05_coupling_candidate_keeps_the_tf32_bar(clean_table, tmp_path):
         sm.smash_autotune_clear()
         sm.smash_autotune_load(str(path))
         z = h.matvec(_dev(q), precision=sm.SMASH_PREC_TF32).cpu().numpy()
+        assert_entrywise(z, zo, sc, TOL_TF32, what=f"tf32 choice {choice}")
         assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-3, choice
     h.close()
