@@ -195,10 +195,11 @@ struct KsumOzArgs {
     const int32_t *level;
     const uint64_t *cell;
     double *out;               // target vectors (FP64), ldq
-    double scale;              // 1/s (coupling), 2^-e (near field, exact frame)
+    double scale;              // 1/s: entries are taken in the normalised frame
     int ldq, dim;
     // near field only
     const float *xt3, *ys3;    // exact three-float coordinates, 12 floats per point
+    float n3h, n3l;            // 2^e / s as a two-float: exact-frame differences times it are normalised
     int *fallback;             // per CTA: 1 when the node is left to the double-float kernel
     int same;                  // X = Y: a target meets its own point (entry 0)
 };
@@ -209,7 +210,7 @@ struct KsumOzArgs {
 template <int NC, bool NEAR>
 struct OzLayout {
     static constexpr int kCap = NEAR ? 192 : kOzTileCap;  // sources per tile (three CTAs per SM)
-    static constexpr int kCoordF4 = NEAR ? 3 : 2;          // float4 per source: (hi, lo) or (hi, mid, lo)
+    static constexpr int kCoordF4 = 2;                      // float4 per source: normalised (hi, lo)
     static constexpr int kDigitBytes = kOzDigits * NC * 2;
     static constexpr int kStride = kDigitBytes + 16;
     static constexpr size_t kCoords = sizeof(float4) * kCoordF4 * kCap;
@@ -293,7 +294,11 @@ __device__ __forceinline__ int oz_row_exponent(float gap2, double node_kb) {
 // squares exactly by FMA, their sum by magnitude-ordered Fast2Sum (the squares
 // are non-negative, so max/min order them), then one Newton step on the
 // hardware reciprocal square root with the residual 1 - r y0^2 formed by FMA
-// and the result renormalised.
+// and the result renormalised.  The pair (dh, dl) from normalised coordinates
+// is not normalised (|dl| reaches 2^-23 against |dh| >= 2^-8 or so), so r^2's
+// low part rl can be ~2^-15 of rh: the seed is taken at rh + rl, which keeps
+// the residual at the seed's own ~2^-22 and the Newton step's neglected
+// square term below 2^-43.
 template <int D, bool ZERO>
 __device__ __forceinline__ void oz_invr(const float *dh, const float *dl, float &kh, float &kl) {
     float p[3], e[3];
@@ -318,7 +323,7 @@ __device__ __forceinline__ void oz_invr(const float *dh, const float *dl, float 
         kl = 0.f;
         return;
     }
-    const float y0 = rsqrtf(rh);
+    const float y0 = rsqrtf(rh + rl);
     const float th = y0 * y0;
     const float tl = fmaf(y0, y0, -th);
     float ee = fmaf(-rh, th, 1.0f);
@@ -341,15 +346,41 @@ __device__ __forceinline__ void oz_entry(const float4 &xh, const float4 &xl, con
         oz_invr<D, false>(dh, dl, kh, kl);
 }
 
-// the same from exact three-float coordinates (near field: close pairs, and a
-// target's own point, whose entry is 0)
+// Near-field entries (3.20).  The normalised two-float coordinates give a
+// difference to ~2^-46.5 absolute (both coordinates within 2^-48 of x'', the
+// lo parts' difference rounded), i.e. ~2^-38.5 relative at the threshold
+// |d''| = 2^-8, as for the closest admissible pairs of the coupling.  A pair
+// closer than that (rare: a ball of radius 2^-8 of the cube around the
+// target) takes its difference from the exact three-float coordinates
+// instead, converted to the normalised frame by the two-float 2^e / s.  A
+// target's own point and coincident points give the entry 0.
+constexpr float kNearExact2 = 0x1p-16f;  // (2^-8)^2
+
 template <int KID, int D>
-__device__ __forceinline__ void oz_entry3(const float4 *x, const float4 &yh, const float4 &ym, const float4 &yl,
-                                          float &kh, float &kl) {
+__device__ __forceinline__ void oz_entry_near(const float4 &xh, const float4 &xl, const float *x3p,
+                                              const float4 &yh, const float4 &yl, const float *y3p, float n3h,
+                                              float n3l, float &kh, float &kl) {
     float dh[3], dl[3];
-    diff3(x[0].x, x[1].x, x[2].x, yh.x, ym.x, yl.x, dh[0], dl[0]);
-    diff3(x[0].y, x[1].y, x[2].y, yh.y, ym.y, yl.y, dh[1], dl[1]);
-    diff3(x[0].z, x[1].z, x[2].z, yh.z, ym.z, yl.z, dh[2], dl[2]);
+    dh[0] = xh.x - yh.x; dh[1] = xh.y - yh.y; dh[2] = xh.z - yh.z;
+    dl[0] = xl.x - yl.x; dl[1] = xl.y - yl.y; dl[2] = xl.z - yl.z;
+    float d2 = dh[0] * dh[0];
+    if (D > 1) d2 = fmaf(dh[1], dh[1], d2);
+    if (D > 2) d2 = fmaf(dh[2], dh[2], d2);
+    if (d2 < kNearExact2) {
+        const float4 *y3 = reinterpret_cast<const float4 *>(y3p);
+        const float4 yh3 = y3[0], ym3 = y3[1], yl3 = y3[2];
+        const float4 *x3 = reinterpret_cast<const float4 *>(x3p);
+        float eh[3], el[3];
+        diff3(x3[0].x, x3[1].x, x3[2].x, yh3.x, ym3.x, yl3.x, eh[0], el[0]);
+        diff3(x3[0].y, x3[1].y, x3[2].y, yh3.y, ym3.y, yl3.y, eh[1], el[1]);
+        diff3(x3[0].z, x3[1].z, x3[2].z, yh3.z, ym3.z, yl3.z, eh[2], el[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {  // (eh + el)(n3h + n3l), renormalised
+            const float p = eh[a] * n3h;
+            const float e = fmaf(eh[a], n3h, -p);
+            fast_two_sum(p, fmaf(el[a], n3h, fmaf(eh[a], n3l, e)), dh[a], dl[a]);
+        }
+    }
     if (KID == SMASH_K_CAUCHY1D)
         kappa_dd<KID, D>(dh, dl, kh, kl);
     else
@@ -418,13 +449,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
         const int64_t tpt = toff + tb + (tr < tcount ? tr : 0);
         const float4 *px = reinterpret_cast<const float4 *>(a.xt + tpt * 8);
         const float4 xh = px[0], xl = px[1];
-        float4 x3[3];
-        if (NEAR) {
-            const float4 *p3 = reinterpret_cast<const float4 *>(a.xt3 + tpt * 12);
-            x3[0] = p3[0];
-            x3[1] = p3[1];
-            x3[2] = p3[2];
-        }
+        const float *x3p = NEAR ? a.xt3 + tpt * 12 : nullptr;  // exact coordinates, for close pairs
         // first digit: K 2^(8-E); lo(K) enters the fourth digit at 2^24 times that
         float sc0;
         {
@@ -540,7 +565,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                 for (int q = tid; q < NF * fill16; q += kOzThreads) {
                     const int b = q / NF, part = q - b * NF;
                     const int64_t src = sidx[b < fill ? b : 0];
-                    oz_cp16(sy + part * CAP + b, NEAR ? a.ys3 + src * 12 + 4 * part : a.ys + src * 8 + 4 * part);
+                    oz_cp16(sy + part * CAP + b, a.ys + src * 8 + 4 * part);
                 }
                 constexpr int kPieces = Lay::kDigitBytes / 16;
                 for (int q = tid; q < fill * kPieces; q += kOzThreads) {
@@ -563,7 +588,9 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             if (NEAR)
-                                oz_entry3<KID, D>(x3, sy[cs[u]], sy[CAP + cs[u]], sy[2 * CAP + cs[u]], kh[u], kl[u]);
+                                oz_entry_near<KID, D>(xh, xl, x3p, sy[cs[u]], sy[CAP + cs[u]],
+                                                      a.ys3 + sidx[cs[u] < fill ? cs[u] : 0] * 12, a.n3h, a.n3l,
+                                                      kh[u], kl[u]);
                             else
                                 oz_entry<KID, D>(xh, xl, sy[cs[u]], sy[CAP + cs[u]], kh[u], kl[u]);
                         }
@@ -721,10 +748,11 @@ void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, i
 // ------------------------------------------------------------------ near field
 // The near field (3.20) with the same digit-split products: sources are the
 // points of the neighbouring leaves, q the sorted input vectors (one exponent
-// per column), entries from the exact three-float coordinates.  A row's
-// exponent comes from its nearest source; nodes with coincident points or a
-// spread of distances above 2^12 are flagged in `fallback` and left to the
-// double-float kernel.
+// per column), entries from the normalised two-float coordinates, or from the
+// exact three-float ones for the rare pairs closer than 2^-8 of the cube
+// (oz_entry_near).  A row's exponent comes from its nearest source; nodes with
+// coincident points or a spread of distances above 2^12 are flagged in
+// `fallback` and left to the double-float kernel.
 
 // max |q_pc| per column over all points (non-negative doubles order as their bits)
 __global__ void oz_colmax_flat_kernel(const double *__restrict__ q, int64_t n, int ldq,
@@ -792,7 +820,12 @@ void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, 
     a.ptr = h->near_ptr; a.col = h->near_col; a.s_off = h->cs; a.s_cnt = h->cc;
     a.xt = h->xs_dd; a.ys = h->ys_dd; a.xt3 = h->xs_x3; a.ys3 = h->ys_x3;
     a.dig = dig; a.fd = fd; a.colscale = colscale; a.level = h->level; a.cell = h->cell;
-    a.out = zs; a.scale = ldexp(1.0, -h->dd_e); a.ldq = ldq; a.dim = h->dim;
+    a.out = zs; a.scale = 1.0 / h->s; a.ldq = ldq; a.dim = h->dim;
+    {
+        const double nrm = ldexp(1.0, h->dd_e) / h->s;  // in (1/2, 1]
+        a.n3h = (float)nrm;
+        a.n3l = (float)(nrm - (double)a.n3h);
+    }
     a.fallback = fallback; a.same = h->same;
     launch_oz_kernel<true>(h, kid, a, h->nleaves, s);
     tmp.release();
