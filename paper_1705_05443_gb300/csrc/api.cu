@@ -508,7 +508,8 @@ static smash_status matvec_impl(smash_handle h, int kid, const double *X, double
         io.release();
         if (yhost || !stream) {
             CK(cudaStreamSynchronize(s));
-            if (precision == SMASH_PREC_TF32 && tc05_take_timeouts() > 0)
+            if ((precision == SMASH_PREC_TF32 && tc05_take_timeouts() > 0) ||
+                (precision == SMASH_PREC_F32X2 && oz5_take_timeouts() > 0))
                 fail(SMASH_ETIMEOUT, "a tensor-core wait gave up; the result is not valid");
         }
         return SMASH_OK;

@@ -210,10 +210,17 @@ int tc05_take_timeouts();
 // the double-float coupling with its products on the tensor cores (exact
 // 8-bit digit splits of the entries and of q^, FP64 q^ in, FP64 zhat out);
 // supported for one problem of at most 10 levels, tau < 1, ldq <= 16
+// (warp MMAs); with tc05 true the same digit products are issued as tcgen05.mma
+// with the level sums in tensor memory (9..16 columns).  oz5_take_timeouts
+// returns and clears the count of CTAs of that variant whose bounded mbarrier
+// waits gave up.
 bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq);
-void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s);
-// the near field with the same digit-split products (exact three-float
-// coordinates, FP64 q in, zs out); nodes it cannot take get fallback[i] = 1
+void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s,
+                 bool tc05 = false);
+int oz5_take_timeouts();
+// the near field with the same digit-split products (normalised two-float
+// coordinates, exact three-float ones for close pairs, FP64 q in, zs out);
+// nodes it cannot take get fallback[i] = 1
 // (i indexes the leaf list) and must be run by the double-float kernel
 bool near_oz_supported(const smash_h2 *h, int kid, int ldq);
 void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, int *fallback, cudaStream_t s);

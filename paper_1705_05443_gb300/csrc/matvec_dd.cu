@@ -570,8 +570,9 @@ void matvec_dd(const smash_h2 *h, const double *X, double *Y, int nrhs, cudaStre
             char key[128];
             std::snprintf(key, sizeof(key), "coupling_dd/sm%d/k%d/d%d/ld%d/n%lld", h->num_sms, kid, h->dim, ldq,
                           pow2_at_least(h->nnodes));
-            tune_choose(key, {0, 1}, ldq >= 8 ? 0 : 1, s, [&](int c) {
+            tune_choose(key, {0, 1, 2}, ldq >= 8 ? 0 : 1, s, [&](int c) {
                 if (c == 0) coupling_oz(h, kid, qhat, zhat, ldq, s);
+                else if (c == 2) coupling_oz(h, kid, qhat, zhat, ldq, s, true);
                 else dd_coupling();
             });
         } else {

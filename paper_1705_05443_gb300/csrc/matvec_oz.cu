@@ -712,15 +712,470 @@ static void launch_oz_kernel(const smash_h2 *h, int kid, const KsumOzArgs &a, in
         launch_oz_nt<SMASH_K_INVR, 1, NEAR>(a, ntn, s);
 }
 
+// ------------------------------------------------------------------ tcgen05 variant
+// The same digit-split coupling with the digit products issued as tcgen05.mma
+// (kind::f16, bf16 digits, FP32 accumulation in tensor memory) by one thread,
+// instead of warp MMAs:
+//
+//  * D_L = sum_{s+t=L} A_s B_t with M = 64 rows, 16 right-hand sides and K =
+//    the sources of a stage; the six level sums D_0..D_5 take tensor-memory
+//    columns 16 L .. 16 L + 15.  The B planes lie one after another as one
+//    K-major tile of 96 rows, so one MMA per entry digit s and K-step,
+//    A_s [B_0 .. B_{5-s}] with N = 16 (6 - s) written to columns 16 s .. 95,
+//    forms all of A_s's level products (6 MMAs per K-step, not 21).  With
+//    M = 64, row i of D sits in lane 32 (i / 16) + i % 16.
+//  * A_s (entry digit s) is written to shared memory in the canonical K-major
+//    layout without swizzle (8-row x 16-byte core matrices, 128 bytes apart
+//    along K).  A plane holds 2048 entries: 64 target rows x 32 sources, or,
+//    for a pass of at most 32 targets, 32 rows x 64 sources (the MMA's rows
+//    32..63 then read the next plane and are never used), so that the
+//    threads stay busy on the small nodes of the lowest level.  One thread
+//    evaluates 8 entries of one target row (a source octet) into registers
+//    while the previous stage's MMAs run, and stores them, 16 bytes per
+//    digit plane, once those have completed (bounded mbarrier wait).
+//  * B_t (q^ digit t) comes from the staged q^ digits (per source six planes
+//    of 16 bf16, as the warp-MMA kernel reads them) through ldmatrix.trans,
+//    which turns source-major 8 x 8 blocks into K-major core matrices.
+//  * A window of at most 128 sources of one partner level keeps every level
+//    sum below 2^24 (as for the warp-MMA kernel's tiles); at its end the
+//    warps holding rows read D_0..D_5 (tcgen05.ld), fold them into
+//    double-float running sums kept in tensor-memory columns 96 (hi) and
+//    112 (lo), and the next window's first MMA overwrites D.
+// Staging of stage i + 1 (cp.async, warp 0, which also publishes the next
+// stage's geometry) overlaps stage i, and one CTA barrier per stage hands the
+// operands to the issuing thread.  Every wait on the tensor cores is bounded;
+// a CTA that gives up counts a timeout, stops (all its threads together),
+// frees its tensor memory and returns, and CTAs that start after a timeout
+// return at once: the host rejects the result.
+constexpr int k5M = 64;            // MMA M: target rows per pass
+constexpr int k5N = 16;            // right-hand sides (digits past ldq are zero)
+constexpr int k5PlaneEntries = 2048;
+constexpr int k5MaxStage = 64;     // sources per stage at most (passes of <= 32 targets)
+constexpr int k5Win = 128;         // sources per accumulation window
+constexpr int k5RawStride = 192;   // bytes per staged source: 6 planes x 16 bf16 digits
+constexpr long k5MaxSpin = 1L << 22;
+constexpr uint32_t k5Cols = 128;   // tensor-memory columns: D_L at 16 L, sums at 96 (hi) and 112 (lo)
+
+__device__ int g_oz5_timeouts;
+
+struct Oz5Layout {
+    static constexpr int kAPlane = k5PlaneEntries * 2;           // 4 KB per entry-digit plane
+    static constexpr int kBPlane = k5N * k5MaxStage * 2;         // 2 KB per q^-digit plane (at most)
+    static constexpr int kA = kOzDigits * kAPlane;
+    static constexpr int kB = kOzDigits * kBPlane;
+    static constexpr int kRaw = k5MaxStage * k5RawStride;
+    static constexpr int kY = k5MaxStage * 32;                    // (hi, lo) float4 per source
+    static constexpr int kStaging = kRaw + kY;
+    static constexpr int kT = k5M * 32;                           // target (hi, lo) float4
+    static constexpr int bytes = kA + kB + 2 * kStaging + kT + k5M * 8;
+    static_assert(kA % 1024 == 0 && kB % 1024 == 0 && kStaging % 16 == 0, "aligned regions");
+};
+
+__device__ __forceinline__ uint32_t oz5_su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, LBO 128 B (next core matrix
+// along K), SBO sbo bytes (next 8-row group)
+__device__ __forceinline__ uint64_t oz5_desc(uint32_t saddr, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ bool oz5_wait(uint32_t mbar, uint32_t parity) {
+    for (long it = 0; it < k5MaxSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void oz5_ld4(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void oz5_st4(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])));
+}
+
+// stage geometry at stream position pos of the chunk: its partner level and
+// the sources it takes (up to kst, never past the level run)
+__device__ __forceinline__ void oz5_stage(const PartnerChunk &pc, const int *plev, const int *runend, int pos,
+                                          int kst, int &lv, int &fill) {
+    int plo = 0, phi = pc.n - 1;
+    while (plo < phi) {
+        const int mid = (plo + phi + 1) >> 1;
+        if (pc.pre[mid] <= pos) plo = mid;
+        else phi = mid - 1;
+    }
+    lv = plev[plo];
+    fill = min(kst, pc.pre[runend[plo]] - pos);
+}
+
+// warps 0 and 1 gather a stage: thread k < 64 copies the digits and
+// coordinates of source k (when below fill)
+__device__ __forceinline__ void oz5_stage_load(const KsumOzArgs &a, const PartnerChunk &pc, int pos, int fill,
+                                               unsigned char *buf) {
+    const int k = threadIdx.x;
+    if (k < fill) {
+        const int64_t src = chunk_source(pc, pos + k);
+        const unsigned char *dg = reinterpret_cast<const unsigned char *>(a.dig) + src * k5RawStride;
+#pragma unroll
+        for (int p = 0; p < k5RawStride / 16; ++p) oz_cp16(buf + k * k5RawStride + 16 * p, dg + 16 * p);
+        float *y = reinterpret_cast<float *>(buf + Oz5Layout::kRaw) + k * 8;
+        oz_cp16(y, a.ys + src * 8);
+        oz_cp16(y + 4, a.ys + src * 8 + 4);
+    }
+}
+
+// fold D_0..D_5 of the lane's row into its double-float sums (lanes 0-15 of
+// the warp hold rows; the other lanes fold unused data)
+__device__ __forceinline__ void oz5_flush(uint32_t tmem, const int *sfd, int lv) {
+    const uint32_t lb = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < k5N; c0 += 4) {
+        uint32_t C[kOzDigits][4], H[4], Lw[4];
+#pragma unroll
+        for (int L = 0; L < kOzDigits; ++L) oz5_ld4(lb + 16 * L + c0, C[L]);
+        oz5_ld4(lb + 96 + c0, H);
+        oz5_ld4(lb + 112 + c0, Lw);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float ah[4], al[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float fac = ldexpf(1.0f, sfd[lv * 16 + c0 + j]);
+            const float c[kOzDigits] = {__uint_as_float(C[0][j]), __uint_as_float(C[1][j]), __uint_as_float(C[2][j]),
+                                        __uint_as_float(C[3][j]), __uint_as_float(C[4][j]), __uint_as_float(C[5][j])};
+            const float tail = fmaf(c[5], 1.0f / 65536.0f, fmaf(c[4], 1.0f / 256.0f, c[3]));
+            float h, l, e2, e3;
+            two_sum_ordered(c[0], c[1] * (1.0f / 256.0f), h, l);
+            two_sum_ordered(h, c[2] * (1.0f / 65536.0f), h, e2);
+            l = fmaf(tail, 1.0f / 16777216.0f, l + e2);
+            float sh = __uint_as_float(H[j]), sl = __uint_as_float(Lw[j]);
+            two_sum_ordered(sh, h * fac, sh, e3);
+            sl = sl + (e3 + l * fac);
+            fast_two_sum(sh, sl, ah[j], al[j]);
+        }
+        oz5_st4(lb + 96 + c0, ah);
+        oz5_st4(lb + 112 + c0, al);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int KID, int D>
+__global__ void __launch_bounds__(kOzThreads, 3) ksum_oz5_kernel(KsumOzArgs a) {
+    using Lay = Oz5Layout;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ PartnerChunk pc;
+    __shared__ unsigned long long bound_slot;
+    __shared__ int runend[kPartnerChunk];
+    __shared__ int plev[kPartnerChunk];
+    __shared__ int sfd[kOzLevels * 16];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_skip;
+    __shared__ int s_geo[2][2];  // (level, fill) of the next stage, by stage parity
+    unsigned char *sA = smraw;
+    unsigned char *sB = smraw + Lay::kA;
+    unsigned char *stg0 = smraw + Lay::kA + Lay::kB;
+    float4 *tx = reinterpret_cast<float4 *>(stg0 + 2 * Lay::kStaging);
+    float *sc0s = reinterpret_cast<float *>(tx + 2 * k5M);
+    int *rowE = reinterpret_cast<int *>(sc0s + k5M);
+
+    const int64_t g = a.tnodes[blockIdx.x];
+    const int T = a.t_cnt[g];
+    if (threadIdx.x == 0) s_skip = *reinterpret_cast<volatile int *>(&g_oz5_timeouts);
+    __syncthreads();
+    if (T == 0 || s_skip != 0) return;
+    const int64_t toff = a.t_off[g];
+    const int64_t e0 = a.ptr[g], e1 = a.ptr[g + 1];
+    const int ldq = a.ldq;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kOzLevels * 16; i += kOzThreads) sfd[i] = a.fd[i];
+    const double kb_node = oz_node_bound(a, g, e0, e1, &bound_slot);
+    if (!(kb_node < INFINITY)) {
+        for (int q = tid; q < T * ldq; q += kOzThreads) a.out[toff * ldq + q] = NAN;
+        return;
+    }
+    // operand and staging regions start at 0 (stale contents stay finite)
+    for (int i = tid; i < (Lay::kA + Lay::kB + 2 * Lay::kStaging) / 16; i += kOzThreads)
+        reinterpret_cast<uint4 *>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz5_su32(&mbar)));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz5_su32(&tslot)),
+                     "r"(k5Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tslot;
+    const uint32_t mb = oz5_su32(&mbar);
+    int nst = 0;             // stages committed by this CTA
+    bool pending = false;    // the last committed stage has not been waited for
+    bool timed_out = false;  // block-uniform: a wait gave up
+
+    for (int tb = 0; tb < T && !timed_out; tb += k5M) {
+        const int tcount = min(k5M, T - tb);
+        // plane shape of the pass: rows x kst sources (kst / 16 K-steps)
+        const int rows = tcount <= 32 ? 32 : 64;
+        const int kst = k5PlaneEntries / rows;
+        const uint32_t sbo_a = (uint32_t)(kst / 8) * 128u;  // also B's row-group stride
+        const int nitems = tcount * (kst / 8);
+        const int row = tid < nitems ? tid % tcount : 0, oct = tid < nitems ? tid / tcount : 0;
+        const int fwarps = (tcount + 15) / 16;  // warps whose lanes 0-15 hold rows
+        const uint64_t desc_a = oz5_desc(oz5_su32(sA), sbo_a), desc_b = oz5_desc(oz5_su32(sB), sbo_a);
+        for (int q = tid; q < 2 * tcount; q += kOzThreads)
+            tx[q] = reinterpret_cast<const float4 *>(a.xt + (toff + tb + (q >> 1)) * 8)[q & 1];
+        __syncthreads();
+        // row exponents: the four lanes of a quad split the row's partners
+        for (int r0 = 0; r0 < tcount; r0 += kOzThreads / 4) {
+            const int rr = r0 + (tid >> 2);
+            const float4 xh = tx[2 * (rr < tcount ? rr : 0)];
+            const float gap2 = oz_point_gap2<D>(xh, a, e0, e1, tid & 3);
+            if (rr < tcount && (tid & 3) == 0) {
+                const int E = oz_row_exponent(gap2, kb_node);
+                rowE[rr] = E;
+                sc0s[rr] = ldexpf(1.0f, 8 - E);
+            }
+        }
+        // running sums of the pass start at 0
+        if (warp < 4) {
+            const float z[4] = {0.f, 0.f, 0.f, 0.f};
+            const uint32_t lb = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+            for (int c = 96; c < 128; c += 4) oz5_st4(lb + c, z);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        __syncthreads();
+        int win = 0, wlv = -1;
+        for (int64_t e = e0; e < e1 && !timed_out;) {
+            load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
+            const int nchunk = pc.n, total = pc.pre[pc.n];
+            for (int q = tid; q < nchunk; q += kOzThreads) plev[q] = a.level[a.col[e + q]];
+            __syncthreads();
+            if (tid == 0) {
+                int end = nchunk;
+                for (int p = nchunk - 1; p >= 0; --p) {
+                    if (p + 1 < nchunk && plev[p + 1] != plev[p]) end = p + 1;
+                    runend[p] = end;
+                }
+            }
+            __syncthreads();
+            e += nchunk;
+            int pos = 0, cur = 0, lv, fill;
+            oz5_stage(pc, plev, runend, 0, kst, lv, fill);
+            oz5_stage_load(a, pc, 0, fill, stg0);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            while (pos < total) {
+                unsigned char *buf = stg0 + cur * Lay::kStaging;
+                const int npos = pos + fill;
+                // warp 0: the next stage's geometry (published at this stage's
+                // barrier) and its data, into the other buffer (free: its last
+                // reads came before the previous stage's barrier)
+                if (warp < 2) {
+                    int nlv = 0, nfill = 0;
+                    if (npos < total) {
+                        oz5_stage(pc, plev, runend, npos, kst, nlv, nfill);
+                        oz5_stage_load(a, pc, npos, nfill, stg0 + (cur ^ 1) * Lay::kStaging);
+                    }
+                    if (tid == 0) {
+                        s_geo[nst & 1][0] = nlv;
+                        s_geo[nst & 1][1] = nfill;
+                    }
+                }
+                const bool fresh = win == 0 || lv != wlv || win + fill > k5Win;
+                // the entries of one (row, source octet) per thread, digits packed in registers
+                const bool has = tid < nitems;
+                uint32_t w[kOzDigits][4];
+                if (has) {
+                    const float4 xh = tx[2 * row], xl = tx[2 * row + 1];
+                    const float sc0 = sc0s[row];
+                    const float4 *cy = reinterpret_cast<const float4 *>(buf + Lay::kRaw);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float kh[2], kl[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int k = 8 * oct + 2 * j + u;
+                            kh[u] = 0.f;
+                            kl[u] = 0.f;
+                            if (k < fill) oz_entry<KID, D>(xh, xl, cy[2 * k], cy[2 * k + 1], kh[u], kl[u]);
+                        }
+                        float r[2];
+#pragma unroll
+                        for (int s = 0; s < kOzDigits; ++s) {
+                            float dg[2];
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                if (s == 0) {
+                                    dg[u] = fmaf(kh[u], sc0, kOzShift) - kOzShift;
+                                    r[u] = fmaf(kh[u], sc0, -dg[u]);
+                                } else if (s == 3) {
+                                    const float x = fmaf(r[u], 256.0f, kl[u] * (sc0 * 16777216.0f));
+                                    dg[u] = (x + kOzShift) - kOzShift;
+                                    r[u] = x - dg[u];
+                                } else {
+                                    dg[u] = fmaf(r[u], 256.0f, kOzShift) - kOzShift;
+                                    r[u] = fmaf(r[u], 256.0f, -dg[u]);
+                                }
+                            }
+                            w[s][j] = oz_pack(dg[0], dg[1]);
+                        }
+                    }
+                }
+                // the previous stage's MMAs are done: operands free, D readable
+                bool ok = true;
+                if (pending) {
+                    ok = oz5_wait(mb, (uint32_t)((nst - 1) & 1));
+                    pending = false;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (fresh && win > 0 && warp < fwarps) oz5_flush(tmem, sfd, wlv);
+                if (fresh) {
+                    win = 0;
+                    wlv = lv;
+                }
+                win += fill;
+                if (has) {
+                    const uint32_t off = (uint32_t)(row >> 3) * sbo_a + (uint32_t)oct * 128u + (uint32_t)(row & 7) * 16u;
+#pragma unroll
+                    for (int s = 0; s < kOzDigits; ++s)
+                        *reinterpret_cast<uint4 *>(sA + s * Lay::kAPlane + off) =
+                            make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                }
+                {
+                    // B: per (plane t, column octet o, 32-source block) four 8 x 8
+                    // source-major matrices, transposed into K-major core matrices;
+                    // the 12 (t, o) pairs of a block are spread over the warps
+                    const uint32_t src0 = oz5_su32(buf) + (uint32_t)lane * k5RawStride;
+                    unsigned char *dst0 = sB + (lane >> 2) * 16 + (lane & 3) * 4;
+                    for (int sb = 0; sb < kst / 32; ++sb)
+                        for (int to = warp; to < 2 * kOzDigits; to += kOzThreads / 32) {
+                            // to = 2 t + o: plane t, column octet o
+                            uint32_t R0, R1, R2, R3;
+                            oz_ldsm_x4_trans(src0 + (uint32_t)(32 * sb) * k5RawStride + (uint32_t)to * 16, R0, R1,
+                                             R2, R3);
+                            unsigned char *dst = dst0 + (uint32_t)to * sbo_a + (uint32_t)(4 * sb) * 128u;
+                            *reinterpret_cast<uint32_t *>(dst) = R0;
+                            *reinterpret_cast<uint32_t *>(dst + 128) = R1;
+                            *reinterpret_cast<uint32_t *>(dst + 256) = R2;
+                            *reinterpret_cast<uint32_t *>(dst + 384) = R3;
+                        }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("cp.async.wait_all;" ::: "memory");  // the next stage's data (warp 0)
+                if (__syncthreads_or(!ok)) {
+                    timed_out = true;
+                    break;
+                }
+                if (tid == kOzThreads - 1) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int ks = 0; ks < kst / 16; ++ks)
+#pragma unroll
+                        for (int s = 0; s < kOzDigits; ++s) {
+                            // the address field counts 16-byte units (no carry out of it)
+                            const uint64_t ad = desc_a + (uint64_t)((s * Lay::kAPlane + ks * 256) >> 4);
+                            const uint64_t bd = desc_b + (uint64_t)((ks * 256) >> 4);
+                            // BF16 x BF16 -> F32, both K-major, M = 64, N = 16 (6 - s)
+                            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                                   ((uint32_t)(k5N * (kOzDigits - s) >> 3) << 17) |
+                                                   ((uint32_t)(k5M >> 4) << 24);
+                            const uint32_t en = (fresh && ks == 0 && s == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                    tmem + (uint32_t)(16 * s)),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(en));
+                        }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                        : "memory");
+                }
+                pending = true;
+                pos = npos;
+                lv = s_geo[nst & 1][0];
+                fill = s_geo[nst & 1][1];
+                ++nst;
+                cur ^= 1;
+            }
+        }
+        if (timed_out) break;
+        // last window of the pass, then the rows' sums scaled out
+        bool ok = true;
+        if (pending) {
+            ok = oz5_wait(mb, (uint32_t)((nst - 1) & 1));
+            pending = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp < fwarps) {
+            if (win > 0) oz5_flush(tmem, sfd, wlv);
+            const uint32_t lb = tmem + ((uint32_t)(32 * warp) << 16);
+            uint32_t H[k5N], Lw[k5N];
+#pragma unroll
+            for (int c = 0; c < k5N; c += 4) {
+                oz5_ld4(lb + 96 + c, H + c);
+                oz5_ld4(lb + 112 + c, Lw + c);
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int orow = 16 * warp + lane;
+            if (lane < 16 && orow < tcount) {
+                const double sc = ldexp(a.scale, rowE[orow] - 16);
+#pragma unroll
+                for (int c = 0; c < k5N; ++c)
+                    if (c < ldq)
+                        a.out[(toff + tb + orow) * ldq + c] =
+                            ((double)__uint_as_float(H[c]) + (double)__uint_as_float(Lw[c])) * sc * a.colscale[c];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!ok)) timed_out = true;
+    }
+    if (timed_out && tid == 0) atomicAdd(&g_oz5_timeouts, 1);
+    asm volatile("cp.async.wait_all;" ::: "memory");  // a stopped CTA's prefetch
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(k5Cols));
+}
+
+template <int KID, int D>
+static void launch_oz5(const KsumOzArgs &a, int64_t ntn, cudaStream_t s) {
+    auto kern = ksum_oz5_kernel<KID, D>;
+    allow_max_dynamic_smem((const void *)kern);
+    kern<<<(unsigned)ntn, kOzThreads, Oz5Layout::bytes, s>>>(a);
+    LAUNCHED();
+}
+
+int oz5_take_timeouts() {
+    int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_oz5_timeouts, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (v) cudaMemcpyToSymbol(g_oz5_timeouts, &z, sizeof(int));
+    return v;
+}
+
 bool coupling_oz_supported(const smash_h2 *h, int kid, int ldq) {
     return !dd_exact_coupling(h) && ldq <= 16 && h->tau < 1.0 && h->L < kOzLevels &&
            (kid == SMASH_K_INVR || kid == SMASH_K_CAUCHY1D) && h->nnodes > h->nroots;
 }
 
-void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s) {
+void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, int ldq, cudaStream_t s, bool tc05) {
     const Side &R = h->row;
     const Side &Cs = *h->col;
-    const int NC = ldq <= 8 ? 8 : 16;
+    const int NC = (ldq <= 8 && !tc05) ? 8 : 16;
     const int64_t nsk = std::max<int64_t>(Cs.total_skel, 1);
     Arena tmp(s);
     unsigned long long *cmax = tmp.alloc<unsigned long long>(kOzLevels * 16);
@@ -741,7 +1196,12 @@ void coupling_oz(const smash_h2 *h, int kid, const double *qhat, double *zhat, i
     a.ptr = h->adm_ptr; a.col = h->adm_col; a.s_off = Cs.sk_off; a.s_cnt = Cs.k;
     a.xt = R.skel_dd; a.ys = Cs.skel_dd; a.dig = dig; a.fd = fd; a.colscale = colscale;
     a.level = h->level; a.cell = h->cell; a.out = zhat; a.scale = 1.0 / h->s; a.ldq = ldq; a.dim = h->dim;
-    launch_oz_kernel<false>(h, kid, a, h->nnodes - h->nroots, s);
+    const int64_t ntn = h->nnodes - h->nroots;
+    if (!tc05) launch_oz_kernel<false>(h, kid, a, ntn, s);
+    else if (kid == SMASH_K_CAUCHY1D) launch_oz5<SMASH_K_CAUCHY1D, 1>(a, ntn, s);
+    else if (h->dim == 3) launch_oz5<SMASH_K_INVR, 3>(a, ntn, s);
+    else if (h->dim == 2) launch_oz5<SMASH_K_INVR, 2>(a, ntn, s);
+    else launch_oz5<SMASH_K_INVR, 1>(a, ntn, s);
     tmp.release();
 }
 

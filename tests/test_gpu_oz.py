@@ -1,13 +1,15 @@
 """GPU parity of the coupling with exact digit-split products on the tensor cores.
 
 The double-float matvec (SMASH_PREC_F32X2) computes the coupling (3.19) in one
-of two ways, chosen per launch shape by the tuner (untuned default: the first
+of three ways, chosen per launch shape by the tuner (untuned default: the first
 from 8 columns per pass, else the second):
   0. entries in double-float, entries and q^ split into 8-bit digits whose
-     products are summed exactly on the tensor cores, the digit levels
-     combined in double-float;
-  1. every operation in double-float on the FP32 pipe.
-Both carry ~2^-46 relative precision per entry, so both meet the FP64 bar
+     products are summed exactly on the tensor cores (warp MMAs), the digit
+     levels combined in double-float;
+  1. every operation in double-float on the FP32 pipe;
+  2. as 0, with the digit products issued as tcgen05.mma and the level sums
+     in tensor memory.
+All carry ~2^-46 relative precision per entry, so all meet the FP64 bar
 (entry by entry within 1e-11 of each entry's sum of |terms| against the
 oracle's FP64 H^2 matvec, parity_helpers; relative 2-norm 1e-11 as a second
 line) and agree with each other far below it.  Blocks the digit split does not cover (more than
@@ -72,7 +74,8 @@ def _forced(h, q, table, keys, path, choice):
     return h.matvec(_dev(q), precision=F32X2).cpu().numpy()
 
 
-@pytest.mark.parametrize("d,n,leaf,order,nrhs", [(3, 20000, 128, 4, 16), (3, 9000, 64, 3, 5), (2, 8000, 64, 5, 8),
+@pytest.mark.parametrize("d,n,leaf,order,nrhs", [(3, 20000, 128, 4, 16), (3, 12000, 128, 5, 16), (3, 9000, 64, 3, 5),
+                                                 (2, 8000, 64, 5, 8),
                                                  (2, 6000, 32, 6, 16), (1, 4000, 32, 10, 1), (1, 5000, 64, 8, 12)])
 def test_both_couplings_match_the_oracle(clean_table, tmp_path, d, n, leaf, order, nrhs):
     x = si.uniform_cube(n, d, 6100 + d)
@@ -83,12 +86,16 @@ def test_both_couplings_match_the_oracle(clean_table, tmp_path, d, n, leaf, orde
     assert keys, "the digit-split coupling is offered for this tree"
     z0 = _forced(h, q, table, keys, path, 0)
     z1 = _forced(h, q, table, keys, path, 1)
-    assert_entrywise(z0, zo, sc, TOL_F32X2)
-    assert _rel(z0, zo) <= RTOL
-    assert_entrywise(z1, zo, sc, TOL_F32X2)
-    assert _rel(z1, zo) <= RTOL
-    # the two ways differ only by roundings of the double-float arithmetic
+    z2 = _forced(h, q, table, keys, path, 2)
+    for z, what in ((z0, "warp MMAs"), (z1, "FP32 pipe"), (z2, "tcgen05")):
+        assert_entrywise(z, zo, sc, TOL_F32X2, what=what)
+        assert _rel(z, zo) <= RTOL, what
+    # the ways differ only by roundings of the double-float arithmetic (the
+    # digit products' level sums are exact in both tensor-core variants)
     assert _rel(z0, z1) <= 1e-12
+    assert _rel(z0, z2) <= 1e-12
+    # the tcgen05 variant is deterministic
+    assert np.array_equal(z2, _forced(h, q, table, keys, path, 2))
     h.close()
 
 
@@ -114,7 +121,7 @@ def test_cauchy_rectangular_digit_split(clean_table, tmp_path):
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_CAUCHY1D, 64, 16, 1e-10, y=_dev(y))
     table, keys, path = _coupling_keys(h, q, tmp_path)
     assert keys
-    for choice in (0, 1):
+    for choice in (0, 1, 2):
         z = _forced(h, q, table, keys, path, choice)
         assert_entrywise(z, zo, sc, TOL_F32X2, what=f"choice {choice}")
         assert _rel(z, zo) <= RTOL, choice
@@ -131,13 +138,14 @@ def test_wide_scales_of_q_columns(clean_table, tmp_path):
     zo, sc = oracle_reference(oracle.H2(x, sm.SMASH_K_INVR, 64, 4, 1e-8), q)
     h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
     table, keys, path = _coupling_keys(h, q, tmp_path)
-    z = _forced(h, q, table, keys, path, 0)
-    for c in range(8):
-        if c == 6:
-            assert not np.any(z[:, c])
-        else:
-            assert_entrywise(z[:, c], zo[:, c], sc[:, c], TOL_F32X2, what=f"column {c}")
-            assert _rel(z[:, c], zo[:, c]) <= RTOL, c
+    for choice in (0, 2):
+        z = _forced(h, q, table, keys, path, choice)
+        for c in range(8):
+            if c == 6:
+                assert not np.any(z[:, c])
+            else:
+                assert_entrywise(z[:, c], zo[:, c], sc[:, c], TOL_F32X2, what=f"choice {choice} column {c}")
+                assert _rel(z[:, c], zo[:, c]) <= RTOL, (choice, c)
     h.close()
 
 
