@@ -1027,10 +1027,12 @@ void build_compression(smash_h2 *h, Arena &scratch) {
 // The nearfield block row (side 0) or column (side 1) of each node of a level
 // (3.7)/(3.11) and its truncated SVD by one-sided Jacobi on the rows, in the
 // CPU oracle's order of operations: rounds of disjoint row pairs (the
-// round-robin order of Brent and Luk) spread over the warps, each pair's
-// three dot products summed sequentially by one lane each, the rotation
-// applied element-wise by all lanes.  The kept left singular vectors (above
-// eps_svd of the largest, descending) become extra rows of the node's basis.
+// round-robin order of Brent and Luk) with one thread per pair, which sums
+// its pair's three dot products in ascending order and applies the rotation
+// to its two rows; the pairs of a round are independent, so a round's
+// threads fill a warp (the FP64 pipe charges a warp instruction whatever its
+// active lanes).  The kept left singular vectors (above eps_svd of the
+// largest, descending) become extra rows of the node's basis.
 constexpr int kHssSvdCap = 64;     // singular vectors kept per node at most
 constexpr int kJacobiSweeps = 60;
 constexpr double kJacobiEps = 1e-15;
@@ -1089,12 +1091,11 @@ __global__ void nf_width_kernel(SvdArgs a, int64_t *__restrict__ width) {
 
 template <int NT>
 __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
-    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
     double *sig = reinterpret_cast<double *>(smraw);
     __shared__ int rotated;
     __shared__ int s_sel;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     double *B = a.work + (int64_t)blockIdx.x * a.slot_doubles;
     double *JT = B + a.a_doubles;
     for (int64_t ni = blockIdx.x; ni < a.nl; ni += gridDim.x) {
@@ -1120,7 +1121,7 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
         }
         for (int e = tid; e < m * m; e += NT) JT[e] = (e / m == e % m) ? 1.0 : 0.0;
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0) {  // ||A||_F^2 in the oracle's (row-major) order: it sets the rotation floor
             double f2 = 0.0;
             for (int64_t e = 0; e < (int64_t)m * n; ++e) f2 = __fma_rn(B[e], B[e], f2);
             sig[0] = f2;
@@ -1133,40 +1134,38 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
             if (tid == 0) rotated = 0;
             __syncthreads();
             for (int rr = 0; rr < M - 1; ++rr) {
-                for (int i = warp; i < M / 2; i += NW) {
+                for (int i = tid; i < M / 2; i += NT) {
                     int pa, pb;
                     if (i == 0) { pa = M - 1; pb = rr; }
                     else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
                     const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
                     if (q >= m) continue;
                     double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
-                    double acc = 0.0;
-                    if (lane == 0) for (int e = 0; e < n; ++e) acc = __fma_rn(bp[e], bp[e], acc);
-                    else if (lane == 1) for (int e = 0; e < n; ++e) acc = __fma_rn(bq[e], bq[e], acc);
-                    else if (lane == 2) for (int e = 0; e < n; ++e) acc = __fma_rn(bp[e], bq[e], acc);
-                    const double al = __shfl_sync(0xffffffffu, acc, 0);
-                    const double be = __shfl_sync(0xffffffffu, acc, 1);
-                    const double ga = __shfl_sync(0xffffffffu, acc, 2);
+                    double al = 0.0, be = 0.0, ga = 0.0;
+                    for (int e = 0; e < n; ++e) {
+                        const double u = bp[e], v = bq[e];
+                        al = __fma_rn(u, u, al);
+                        be = __fma_rn(v, v, be);
+                        ga = __fma_rn(u, v, ga);
+                    }
                     const double nab = sqrt(al) * sqrt(be);
                     if (ga == 0.0 || !(fabs(ga) > kJacobiEps * nab) || !(nab > floor_ab)) continue;
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double c = 1.0 / sqrt(1.0 + t * t);
                     const double sn = c * t;
-                    __syncwarp();
-                    for (int e = lane; e < n; e += 32) {
+                    for (int e = 0; e < n; ++e) {
                         const double u = bp[e], v = bq[e];
                         bp[e] = c * u - sn * v;
                         bq[e] = sn * u + c * v;
                     }
                     double *jp = JT + (int64_t)p * m, *jq = JT + (int64_t)q * m;
-                    for (int e = lane; e < m; e += 32) {
+                    for (int e = 0; e < m; ++e) {
                         const double u = jp[e], v = jq[e];
                         jp[e] = c * u - sn * v;
                         jq[e] = sn * u + c * v;
                     }
-                    if (lane == 0) rotated = 1;
-                    __syncwarp();
+                    rotated = 1;
                 }
                 __syncthreads();
             }
@@ -1359,11 +1358,13 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             v.st_stride = (int64_t)kHssSvdCap * m_cap;
             stbuf[i] = scratch.alloc<double>((size_t)nl * v.st_stride);
             v.ST = stbuf[i];
-            constexpr int NT = 128;
-            // slots of at most 256 MiB in all; at least one CTA per SM
+            // one warp per node: a round's pairs (one thread each) fill it for
+            // working sets up to 64; slots of at most 256 MiB in all, at least
+            // one CTA per SM
+            constexpr int NT = 32;
             const int64_t fit = std::max<int64_t>(1, (int64_t)(256ll << 20) / (v.slot_doubles * 8));
             const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nl, std::max<int64_t>(
-                                                                                std::min<int64_t>(fit, 4 * h->num_sms),
+                                                                                std::min<int64_t>(fit, 16 * h->num_sms),
                                                                                 h->num_sms)));
             double *slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
             v.work = slots;
