@@ -843,6 +843,8 @@ def bench_ours(args, w):
             sm.smash_free(h)
         return ms, first
 
+    if args.coupling != "auto":
+        sm.smash_autotune_force("coupling_dd/", {"warp": 0, "fp32": 1, "tcgen05": 2}[args.coupling])
     sm.smash_set_profiling(True)
     # the first warm-up step times the candidate launch shapes of every tuned
     # site (autotuner); later steps use the recorded choices
@@ -1000,6 +1002,7 @@ def bench_ours(args, w):
                                                      3: "1/(x-y)"}[w["kernel"]],
                    "leaf": w["leaf"], "order": w["order"], "tol": w["tol"], "nrhs": nrhs, "tau": 0.7,
                    "precision": "build fp64; matvec " + PREC_TEXT[prec],
+                   "coupling": args.coupling,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{ws}"},
         "roofline": roofline,
@@ -1013,7 +1016,8 @@ def bench_ours(args, w):
                                            "coupling_pairs", "near_pairs", "swaps")},
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(x_np.nbytes + q_np.nbytes), "d2h_bytes_per_step": int(q_np.nbytes)},
-        "gpu_launches": int(launches / args.steps),
+        "gpu_launches": int(launches),  # library kernels launched in the timed region (all K steps)
+        "gpu_launches_per_step": int(launches / args.steps),
         "order_sweep": sweep,
         "taylor_table_6_1": taylor,
         "hss": hss,
@@ -1068,6 +1072,9 @@ def main():
                     help="skip the oracle and dense error columns (spawned CPU processes)")
     ap.add_argument("--no-openmp-baseline", dest="openmp_baseline", action="store_false",
                     help="skip the multi-threaded oracle run of the CPU baseline")
+    ap.add_argument("--coupling", default="auto", choices=["auto", "warp", "tcgen05", "fp32"],
+                    help="pin the double-float coupling: digit products by warp MMAs or by tcgen05.mma, "
+                         "or every operation on the FP32 pipe (default: the tuner's choice)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the default launch shapes instead of tuning them in the first warm-up step")
     args = ap.parse_args()

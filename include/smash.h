@@ -502,6 +502,14 @@ SMASH_API int smash_suggest_rank(double eps, double tau);
  *                          malformed; the table is unchanged)
  *   smash_autotune_save    SMASH_EINVAL if the file cannot be written
  *   smash_autotune_lookup  1 and *value if key has an entry, else 0
+ *   smash_autotune_force   every site whose key starts with prefix takes
+ *                          candidate value (when it is one of the site's
+ *                          candidates), before the table and the timing; a
+ *                          value < 0 removes the prefix's override.  Keys of
+ *                          the double-float coupling start with "coupling_dd/"
+ *                          (0 digit products by warp MMAs, 1 all on the FP32
+ *                          pipe, 2 digit products by tcgen05.mma); of its near
+ *                          field, "near_dd/" (0 digit split, 1 FP32 pipe).
  */
 SMASH_API void smash_set_autotune(int on);
 SMASH_API int smash_autotune_load(const char *path);
@@ -509,6 +517,7 @@ SMASH_API smash_status smash_autotune_save(const char *path);
 SMASH_API int smash_autotune_entries(void);
 SMASH_API void smash_autotune_clear(void);
 SMASH_API int smash_autotune_lookup(const char *key, int *value);
+SMASH_API void smash_autotune_force(const char *prefix, int value);
 
 /*
  * smash_measure_fma_peak -- measured arithmetic peak of the current device in

@@ -24,6 +24,7 @@ __all__ = [
     "smash_matvec_graph", "smash_matvec_graph_count", "smash_matvec_cauchy_like", "smash_matvec_kernel",
     "smash_matvec_double_layer", "SMASH_K_DLP1", "SMASH_K_DLP2", "smash_set_autotune", "smash_autotune_load",
     "smash_autotune_save", "smash_autotune_entries", "smash_autotune_clear", "smash_autotune_lookup",
+    "smash_autotune_force",
     "smash_matvec_noalloc", "smash_near_fallback_leaves", "smash_build_taylor", "smash_matvec_complex",
     "smash_build_hss", "smash_export_hss",
     "SMASH_K_CAUCHY_C", "smash_measure_fma_peak", "smash_node_ranks", "smash_free",
@@ -139,6 +140,8 @@ def load_library(build: bool = True):
     lib.smash_autotune_clear.restype = None
     lib.smash_autotune_lookup.argtypes = [C.c_char_p, C.POINTER(i32)]
     lib.smash_autotune_lookup.restype = i32
+    lib.smash_autotune_force.argtypes = [C.c_char_p, i32]
+    lib.smash_autotune_force.restype = None
     lib.smash_matvec.argtypes = [P, P, P, i32]
     lib.smash_matvec.restype = i32
     lib.smash_matvec_ex.argtypes = [P, P, P, i32, i32, P]
@@ -422,6 +425,12 @@ def smash_autotune_entries() -> int:
 
 def smash_autotune_clear():
     load_library().smash_autotune_clear()
+
+
+def smash_autotune_force(prefix: str, value: int):
+    """Every tuned site whose key starts with prefix takes candidate value
+    (when valid there); value < 0 removes the override."""
+    load_library().smash_autotune_force(prefix.encode(), int(value))
 
 
 def smash_autotune_lookup(key: str):

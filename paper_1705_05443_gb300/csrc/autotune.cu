@@ -23,6 +23,7 @@ namespace smash {
 namespace {
 std::mutex g_mu;
 std::map<std::string, int> g_table;
+std::map<std::string, int> g_force;  // key prefix -> forced candidate
 std::atomic<int> g_mode{0};
 bool g_env_loaded = false;
 
@@ -119,6 +120,18 @@ float tune_time(cudaStream_t s, const std::function<void()> &launch, int reps) {
 int tune_choose(const std::string &key, const std::vector<int> &cands, int dflt, cudaStream_t s,
                 const std::function<void(int)> &launch) {
     int v = dflt;
+    {
+        int forced = -1;
+        {
+            std::lock_guard<std::mutex> lock(g_mu);
+            for (auto &kv : g_force)
+                if (key.compare(0, kv.first.size(), kv.first) == 0) forced = kv.second;
+        }
+        if (forced >= 0 && std::find(cands.begin(), cands.end(), forced) != cands.end()) {
+            launch(forced);
+            return forced;
+        }
+    }
     if (tune_find(key, v)) {
         if (std::find(cands.begin(), cands.end(), v) == cands.end()) v = dflt;  // stale entry
         launch(v);
@@ -189,6 +202,13 @@ smash_status smash_autotune_save(const char *path) {
     }
     f << "\n}}\n";
     return f ? SMASH_OK : SMASH_EINVAL;
+}
+
+void smash_autotune_force(const char *prefix, int value) {
+    if (!prefix) return;
+    std::lock_guard<std::mutex> lock(smash::g_mu);
+    if (value < 0) smash::g_force.erase(prefix);
+    else smash::g_force[prefix] = value;
 }
 
 int smash_autotune_lookup(const char *key, int *value) {

@@ -97,8 +97,14 @@ struct Smem {
     double *W;      // r * m_cap when in shared memory
 };
 
+// a before b: larger value, ties to the lower index.  The values compared are
+// non-negative finite doubles (squared norms, the swap test) or the sentinel
+// -1, whose bit patterns order as signed 64-bit integers exactly as the values
+// do (no -0 arises: every value is a sum of squares starting at +0), so the
+// test runs on the integer pipe rather than GB300's narrow FP64 pipe.
 __device__ __forceinline__ bool better(double a, int64_t ia, double b, int64_t ib) {
-    return a > b || (a == b && ia < ib);
+    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+    return ka > kb || (ka == kb && ia < ib);
 }
 
 // block-wide maximum of (value, index), ties to the lowest index
@@ -1029,10 +1035,11 @@ void build_compression(smash_h2 *h, Arena &scratch) {
 // CPU oracle's order of operations: rounds of disjoint row pairs (the
 // round-robin order of Brent and Luk) with one thread per pair, which sums
 // its pair's three dot products in ascending order and applies the rotation
-// to its two rows; the pairs of a round are independent, so a round's
-// threads fill a warp (the FP64 pipe charges a warp instruction whatever its
-// active lanes).  The kept left singular vectors (above eps_svd of the
-// largest, descending) become extra rows of the node's basis.
+// to its two rows; the pairs of a round are independent and are dealt to the
+// four warps in turn, so that all four FP64 sub-pipes of the SM work on one
+// node (the FP64 pipe charges a warp instruction whatever its active lanes).
+// The kept left singular vectors (above eps_svd of the largest, descending)
+// become extra rows of the node's basis.
 constexpr int kHssSvdCap = 64;     // singular vectors kept per node at most
 constexpr int kJacobiSweeps = 60;
 constexpr double kJacobiEps = 1e-15;
@@ -1134,7 +1141,9 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
             if (tid == 0) rotated = 0;
             __syncthreads();
             for (int rr = 0; rr < M - 1; ++rr) {
-                for (int i = tid; i < M / 2; i += NT) {
+                // pair i of the round goes to lane i / NW of warp i % NW: the
+                // pairs spread over the warps, hence over the SM's sub-partitions
+                for (int i = (tid & 31) * (NT / 32) + (tid >> 5); i < M / 2; i += NT) {
                     int pa, pb;
                     if (i == 0) { pa = M - 1; pb = rr; }
                     else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
@@ -1358,13 +1367,12 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             v.st_stride = (int64_t)kHssSvdCap * m_cap;
             stbuf[i] = scratch.alloc<double>((size_t)nl * v.st_stride);
             v.ST = stbuf[i];
-            // one warp per node: a round's pairs (one thread each) fill it for
-            // working sets up to 64; slots of at most 256 MiB in all, at least
-            // one CTA per SM
-            constexpr int NT = 32;
+            // four warps per node (one per FP64 sub-pipe); slots of at most
+            // 256 MiB in all, at least one CTA per SM
+            constexpr int NT = 128;
             const int64_t fit = std::max<int64_t>(1, (int64_t)(256ll << 20) / (v.slot_doubles * 8));
             const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nl, std::max<int64_t>(
-                                                                                std::min<int64_t>(fit, 16 * h->num_sms),
+                                                                                std::min<int64_t>(fit, 4 * h->num_sms),
                                                                                 h->num_sms)));
             double *slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
             v.work = slots;

@@ -226,3 +226,25 @@ def test_coincident_points_take_the_double_float_near_field(clean_table, tmp_pat
     assert_entrywise(z0, zo, sc, TOL_F32X2)
     assert _rel(z0, zo) <= RTOL
     h.close()
+
+
+def test_forced_coupling_prefix(clean_table, tmp_path):
+    """smash_autotune_force pins every coupling site to one candidate ahead of
+    the table: the tcgen05 variant forced by prefix gives the bits of the
+    same variant chosen through the table, and removing the override returns
+    to the table's choice."""
+    x = si.uniform_cube(9000, 3, 6800)
+    q = si.rhs(9000, 16, 6801)
+    h = sm.H2Matrix(_dev(x), sm.SMASH_K_INVR, 64, 4, 1e-8)
+    table, keys, path = _coupling_keys(h, q, tmp_path)
+    z_table = _forced(h, q, table, keys, path, 2)
+    z_warp = _forced(h, q, table, keys, path, 0)
+    try:
+        sm.smash_autotune_force("coupling_dd/", 2)
+        z_force = h.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    finally:
+        sm.smash_autotune_force("coupling_dd/", -1)
+    assert np.array_equal(z_force, z_table)
+    # the table (all coupling keys at 0) rules again
+    assert np.array_equal(h.matvec(_dev(q), precision=F32X2).cpu().numpy(), z_warp)
+    h.close()
