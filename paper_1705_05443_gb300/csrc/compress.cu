@@ -928,17 +928,17 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
             bool all_in_smem;
             int64_t w_smem_doubles, slot_doubles, x_off;
         };
-        // a candidate is NT + kCpsUnit * c: NT threads per CTA and, for levels
-        // whose largest W does not fit, a W region of 1/c of the opt-in limit
-        // (c CTAs per SM, so that one CTA's serial phases overlap another's
-        // column updates)
+        // a candidate is NT + kCpsUnit * c: NT threads per CTA and, for c > 1,
+        // a W region of 1/c of the opt-in limit (c CTAs per SM, so that one
+        // CTA's serial phases overlap another's column updates); nodes whose
+        // W exceeds the region use the CTA's global slot
         constexpr int kCpsUnit = 4096;
         auto plan = [&](int cand, Plan &pl) -> bool {
             const int NT = cand % kCpsUnit, cps = std::max(1, cand / kCpsUnit);
             size_t base_smem = sizeof(double) * ((size_t)m_cap + 2 * h->r + NT / 32 + 8 + NT / 32) +
                                sizeof(int) * ((size_t)2 * m_cap + NT) + 64;
             size_t w_bytes = sizeof(double) * (size_t)h->r * m_cap;
-            pl.all_in_smem = (base_smem + w_bytes) <= w_smem_limit;
+            pl.all_in_smem = cps == 1 && (base_smem + w_bytes) <= w_smem_limit;
             if (pl.all_in_smem) {
                 pl.w_smem_doubles = (int64_t)h->r * m_cap;
                 pl.x_off = 0;
@@ -976,11 +976,11 @@ static void compress_side(smash_h2 *h, Side &S, bool rows, Arena &scratch) {
             Plan pl;
             if (!plan(nt, pl)) continue;
             cands.push_back(nt);
-            if (!pl.all_in_smem)
-                for (int cps = 2; cps <= 4; cps *= 2) {
-                    Plan p2;
-                    if (plan(nt + kCpsUnit * cps, p2)) cands.push_back(nt + kCpsUnit * cps);
-                }
+            for (int cps = 2; cps <= 8; cps *= 2) {
+                if (nt * cps > 2048) break;  // threads per SM
+                Plan p2;
+                if (plan(nt + kCpsUnit * cps, p2)) cands.push_back(nt + kCpsUnit * cps);
+            }
         }
         auto run = [&](int cand) {
             const int NT = cand % kCpsUnit;
