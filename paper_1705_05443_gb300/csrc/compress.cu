@@ -370,34 +370,47 @@ __global__ void __launch_bounds__(NT) compress_kernel(CompressArgs a) {
         for (;;) {
             if (k == 0 || k == m) break;
             const int mk = m - k;
-            for (int u = tid; u < mk; u += NT)
-                for (int t = k - 1; t >= 0; --t) {
-                    double s = W[(int64_t)t * ld + k + u];
-                    for (int q = t + 1; q < k; ++q) s = __fma_rn(-W[(int64_t)t * ld + q], W[(int64_t)q * ld + k + u], s);
-                    W[(int64_t)t * ld + k + u] = s / W[(int64_t)t * ld + t];
+            // the mk columns of R11^{-1} R12 and the k columns of X = R11^{-1},
+            // one triangular solve per thread (one loop, so that no thread
+            // takes two while others idle)
+            for (int e = tid; e < mk + k; e += NT) {
+                if (e < mk) {
+                    const int u = e;
+                    for (int t = k - 1; t >= 0; --t) {
+                        double s = W[(int64_t)t * ld + k + u];
+                        for (int q = t + 1; q < k; ++q)
+                            s = __fma_rn(-W[(int64_t)t * ld + q], W[(int64_t)q * ld + k + u], s);
+                        W[(int64_t)t * ld + k + u] = s / W[(int64_t)t * ld + t];
+                    }
+                } else {
+                    const int c = e - mk;
+                    for (int t = k - 1; t >= 0; --t) {
+                        double s = (t == c) ? 1.0 : 0.0;
+                        for (int q = t + 1; q < k; ++q)
+                            s = __fma_rn(-W[(int64_t)t * ld + q], X[(int64_t)q * k + c], s);
+                        X[(int64_t)t * k + c] = s / W[(int64_t)t * ld + t];
+                    }
                 }
-            for (int c = tid; c < k; c += NT)
-                for (int t = k - 1; t >= 0; --t) {
-                    double s = (t == c) ? 1.0 : 0.0;
-                    for (int q = t + 1; q < k; ++q) s = __fma_rn(-W[(int64_t)t * ld + q], X[(int64_t)q * k + c], s);
-                    X[(int64_t)t * k + c] = s / W[(int64_t)t * ld + t];
-                }
-            __syncthreads();
-            for (int t = tid; t < k; t += NT) {
-                double s = 0.0;
-                for (int c = 0; c < k; ++c) {
-                    double x = X[(int64_t)t * k + c];
-                    s = __fma_rn(x, x, s);
-                }
-                sh.rho[t] = s;
             }
-            for (int u = tid; u < mk; u += NT) {
+            __syncthreads();
+            // rho_t (row norms of X) and gamma_u^2 (norms of the rest of the
+            // columns of R22), again one per thread
+            for (int e = tid; e < k + mk; e += NT) {
                 double s = 0.0;
-                for (int i = k; i < rr; ++i) {
-                    double x = W[(int64_t)i * ld + k + u];
-                    s = __fma_rn(x, x, s);
+                if (e < k) {
+                    for (int c = 0; c < k; ++c) {
+                        double x = X[(int64_t)e * k + c];
+                        s = __fma_rn(x, x, s);
+                    }
+                    sh.rho[e] = s;
+                } else {
+                    const int u = e - k;
+                    for (int i = k; i < rr; ++i) {
+                        double x = W[(int64_t)i * ld + k + u];
+                        s = __fma_rn(x, x, s);
+                    }
+                    sh.nrm2[u] = s;  // gamma_u^2
                 }
-                sh.nrm2[u] = s;  // gamma_u^2
             }
             __syncthreads();
             double best = -1.0;
