@@ -1046,13 +1046,14 @@ void build_compression(smash_h2 *h, Arena &scratch) {
 // The nearfield block row (side 0) or column (side 1) of each node of a level
 // (3.7)/(3.11) and its truncated SVD by one-sided Jacobi on the rows, in the
 // CPU oracle's order of operations: rounds of disjoint row pairs (the
-// round-robin order of Brent and Luk) with one thread per pair, which sums
-// its pair's three dot products in ascending order and applies the rotation
-// to its two rows; the pairs of a round are independent and are dealt to the
-// four warps in turn, so that all four FP64 sub-pipes of the SM work on one
-// node (the FP64 pipe charges a warp instruction whatever its active lanes).
-// The kept left singular vectors (above eps_svd of the largest, descending)
-// become extra rows of the node's basis.
+// round-robin order of Brent and Luk).  A round runs in two phases: one
+// thread per pair (the pairs dealt to the four warps in turn) sums the pair's
+// three dot products in ascending order and decides its rotation; then every
+// thread applies the rotations element by element, a warp per pair and its
+// lanes along the rows (each element is computed exactly as the oracle does,
+// so the order of elements is free).  The dot products are the only
+// sequential chains left.  The kept left singular vectors (above eps_svd of
+// the largest, descending) become extra rows of the node's basis.
 constexpr int kHssSvdCap = 64;     // singular vectors kept per node at most
 constexpr int kJacobiSweeps = 60;
 constexpr double kJacobiEps = 1e-15;
@@ -1071,6 +1072,7 @@ struct SvdArgs {
     const int64_t *nf_ptr;
     const int32_t *nf_col;
     double eps_svd;
+    int m_cap;                         // largest working set of the level (sizes the round's records)
     double *work;
     int64_t slot_doubles;
     int64_t a_doubles;                 // m_cap * n_cap: JT follows A in a slot
@@ -1112,10 +1114,13 @@ __global__ void nf_width_kernel(SvdArgs a, int64_t *__restrict__ width) {
 template <int NT>
 __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double *sig = reinterpret_cast<double *>(smraw);
+    double *sig = reinterpret_cast<double *>(smraw);  // m_cap
+    // the rotations of a round: (c, s) and the rows (p, q); p = -1 for none
+    double *rot_c = sig + a.m_cap, *rot_s = rot_c + a.m_cap / 2 + 1;
+    int *rot_p = reinterpret_cast<int *>(rot_s + a.m_cap / 2 + 1), *rot_q = rot_p + a.m_cap / 2 + 1;
     __shared__ int rotated;
     __shared__ int s_sel;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *B = a.work + (int64_t)blockIdx.x * a.slot_doubles;
     double *JT = B + a.a_doubles;
     for (int64_t ni = blockIdx.x; ni < a.nl; ni += gridDim.x) {
@@ -1154,15 +1159,17 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
             if (tid == 0) rotated = 0;
             __syncthreads();
             for (int rr = 0; rr < M - 1; ++rr) {
-                // pair i of the round goes to lane i / NW of warp i % NW: the
-                // pairs spread over the warps, hence over the SM's sub-partitions
+                // (1) pair i of the round, one thread each (dealt to the warps in
+                // turn): its three dot products in the oracle's order and the
+                // rotation it calls for
                 for (int i = (tid & 31) * (NT / 32) + (tid >> 5); i < M / 2; i += NT) {
                     int pa, pb;
                     if (i == 0) { pa = M - 1; pb = rr; }
                     else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
                     const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
+                    rot_p[i] = -1;
                     if (q >= m) continue;
-                    double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
+                    const double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
                     double al = 0.0, be = 0.0, ga = 0.0;
                     for (int e = 0; e < n; ++e) {
                         const double u = bp[e], v = bq[e];
@@ -1175,19 +1182,32 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double c = 1.0 / sqrt(1.0 + t * t);
-                    const double sn = c * t;
-                    for (int e = 0; e < n; ++e) {
+                    rot_c[i] = c;
+                    rot_s[i] = c * t;
+                    rot_p[i] = p;
+                    rot_q[i] = q;
+                    rotated = 1;
+                }
+                __syncthreads();
+                // (2) the rotations, element by element over all threads (each
+                // element's two products and difference as in the oracle)
+                for (int i = warp; i < M / 2; i += NT / 32) {
+                    const int p = rot_p[i];
+                    if (p < 0) continue;
+                    const int q = rot_q[i];
+                    const double c = rot_c[i], sn = rot_s[i];
+                    double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
+                    for (int e = lane; e < n; e += 32) {
                         const double u = bp[e], v = bq[e];
                         bp[e] = c * u - sn * v;
                         bq[e] = sn * u + c * v;
                     }
                     double *jp = JT + (int64_t)p * m, *jq = JT + (int64_t)q * m;
-                    for (int e = 0; e < m; ++e) {
+                    for (int e = lane; e < m; e += 32) {
                         const double u = jp[e], v = jq[e];
                         jp[e] = c * u - sn * v;
                         jq[e] = sn * u + c * v;
                     }
-                    rotated = 1;
                 }
                 __syncthreads();
             }
@@ -1389,7 +1409,9 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
                                                                                 h->num_sms)));
             double *slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
             v.work = slots;
-            const size_t smem = sizeof(double) * (size_t)m_cap;
+            v.m_cap = (int)m_cap;
+            const size_t smem = sizeof(double) * (size_t)m_cap + (2 * sizeof(double) + 2 * sizeof(int)) *
+                                                                    (size_t)(m_cap / 2 + 1);
             allow_max_dynamic_smem((const void *)nearfield_svd_kernel<NT>);
             nearfield_svd_kernel<NT><<<(unsigned)grid, NT, smem, st>>>(v);
             LAUNCHED();
