@@ -1046,9 +1046,9 @@ void build_compression(smash_h2 *h, Arena &scratch) {
 // The nearfield block row (side 0) or column (side 1) of each node of a level
 // (3.7)/(3.11) and its truncated SVD by one-sided Jacobi on the rows, in the
 // CPU oracle's order of operations: rounds of disjoint row pairs (the
-// round-robin order of Brent and Luk).  A round runs in two phases: one
-// thread per pair (the pairs dealt to the four warps in turn) sums the pair's
-// three dot products in ascending order and decides its rotation; then every
+// round-robin order of Brent and Luk).  A round runs in three phases: one
+// thread per dot product (three per pair, on neighbouring lanes) sums it in
+// ascending order; one thread per pair decides its rotation; then every
 // thread applies the rotations element by element, a warp per pair and its
 // lanes along the rows (each element is computed exactly as the oracle does,
 // so the order of elements is free).  The dot products are the only
@@ -1116,8 +1116,10 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double *sig = reinterpret_cast<double *>(smraw);  // m_cap
     // the rotations of a round: (c, s) and the rows (p, q); p = -1 for none
-    double *rot_c = sig + a.m_cap, *rot_s = rot_c + a.m_cap / 2 + 1;
-    int *rot_p = reinterpret_cast<int *>(rot_s + a.m_cap / 2 + 1), *rot_q = rot_p + a.m_cap / 2 + 1;
+    const int np_cap = a.m_cap / 2 + 1;  // pairs of a round at most
+    double *rot_c = sig + a.m_cap, *rot_s = rot_c + np_cap;
+    double *dots = rot_s + np_cap;     // [3][np_cap]: alpha, beta, gamma of each pair
+    int *rot_p = reinterpret_cast<int *>(dots + 3 * np_cap), *rot_q = rot_p + np_cap;
     __shared__ int rotated;
     __shared__ int s_sel;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1159,24 +1161,33 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
             if (tid == 0) rotated = 0;
             __syncthreads();
             for (int rr = 0; rr < M - 1; ++rr) {
-                // (1) pair i of the round, one thread each (dealt to the warps in
-                // turn): its three dot products in the oracle's order and the
-                // rotation it calls for
-                for (int i = (tid & 31) * (NT / 32) + (tid >> 5); i < M / 2; i += NT) {
+                // (1) the three dot products of every pair of the round, one
+                // sequential chain per thread in the oracle's order (a pair's
+                // three chains on neighbouring lanes of one warp)
+                const int np = M / 2;
+                for (int it = tid; it < 3 * np; it += NT) {
+                    const int i = it / 3, which = it - 3 * i;
+                    int pa, pb;
+                    if (i == 0) { pa = M - 1; pb = rr; }
+                    else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
+                    const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
+                    if (q >= m) continue;
+                    const double *bu = B + (int64_t)(which == 1 ? q : p) * n;
+                    const double *bv = B + (int64_t)(which == 0 ? p : q) * n;
+                    double acc = 0.0;
+                    for (int e = 0; e < n; ++e) acc = __fma_rn(bu[e], bv[e], acc);
+                    dots[which * np_cap + i] = acc;
+                }
+                __syncthreads();
+                // (1b) each pair's rotation
+                for (int i = tid; i < np; i += NT) {
                     int pa, pb;
                     if (i == 0) { pa = M - 1; pb = rr; }
                     else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
                     const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
                     rot_p[i] = -1;
                     if (q >= m) continue;
-                    const double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
-                    double al = 0.0, be = 0.0, ga = 0.0;
-                    for (int e = 0; e < n; ++e) {
-                        const double u = bp[e], v = bq[e];
-                        al = __fma_rn(u, u, al);
-                        be = __fma_rn(v, v, be);
-                        ga = __fma_rn(u, v, ga);
-                    }
+                    const double al = dots[i], be = dots[np_cap + i], ga = dots[2 * np_cap + i];
                     const double nab = sqrt(al) * sqrt(be);
                     if (ga == 0.0 || !(fabs(ga) > kJacobiEps * nab) || !(nab > floor_ab)) continue;
                     const double zeta = (be - al) / (2.0 * ga);
@@ -1400,9 +1411,10 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             v.st_stride = (int64_t)kHssSvdCap * m_cap;
             stbuf[i] = scratch.alloc<double>((size_t)nl * v.st_stride);
             v.ST = stbuf[i];
-            // four warps per node (one per FP64 sub-pipe); slots of at most
-            // 256 MiB in all, at least one CTA per SM
-            constexpr int NT = 128;
+            // eight warps per node: a round's dot-product chains (three per
+            // pair) fill them; slots of at most 256 MiB in all, at least one CTA
+            // per SM
+            constexpr int NT = 256;
             const int64_t fit = std::max<int64_t>(1, (int64_t)(256ll << 20) / (v.slot_doubles * 8));
             const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nl, std::max<int64_t>(
                                                                                 std::min<int64_t>(fit, 4 * h->num_sms),
@@ -1410,7 +1422,7 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             double *slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
             v.work = slots;
             v.m_cap = (int)m_cap;
-            const size_t smem = sizeof(double) * (size_t)m_cap + (2 * sizeof(double) + 2 * sizeof(int)) *
+            const size_t smem = sizeof(double) * (size_t)m_cap + (5 * sizeof(double) + 2 * sizeof(int)) *
                                                                     (size_t)(m_cap / 2 + 1);
             allow_max_dynamic_smem((const void *)nearfield_svd_kernel<NT>);
             nearfield_svd_kernel<NT><<<(unsigned)grid, NT, smem, st>>>(v);
