@@ -47,8 +47,10 @@ ENTRY_FLOPS = 10
 # DRAM bytes of one digit-split coupling launch (3D 1/r, N = 2^18, 16 RHS,
 # 6.099e9 entries), read and write, from an ncu capture of that launch;
 # scaled to other sizes by the entries of the launch
-OZ_COUPLING_TRAFFIC = (73.693184e6 + 20.957184e6, 6099084090)
+OZ_COUPLING_TRAFFIC = (72.571648e6 + 20.937216e6, 6099084090)
 DD_COUPLING_TRAFFIC = (53.189376e6 + 13.053952e6, 6099084090)
+OZ5_COUPLING_TRAFFIC = (73.001728e6 + 18.445568e6, 6099084090)   # the tcgen05 form, same launch
+COUPLING_NAMES = {0: "digit split, warp MMAs", 1: "double-float on the FP32 pipe", 2: "digit split, tcgen05.mma"}
 HEADLINE_ORACLE_LEAVES = 64   # leaves of the headline compared with the oracle's H^2 matvec
 DENSE_ROWS = 1024             # rows compared with the dense product (O1)
 SWEEP_N = 65536               # order sweep: the 3D 1/r configuration's small size
@@ -69,10 +71,13 @@ def nvtx_range(start: bool, name: str = "smash_timed_steps") -> None:
     except Exception:  # pragma: no cover
         pass
 
-def _coupling_choice(sm, nrhs):
-    """Which double-float coupling ran: the tuner's record (0 digit split on
-    the tensor cores, 1 all on the FP32 pipe), else the untuned default (the
-    digit split from 8 columns per pass)."""
+def _coupling_choice(sm, nrhs, pinned="auto"):
+    """Which double-float coupling ran: the pinned variant, else the tuner's
+    record (0 digit split by warp MMAs, 1 all on the FP32 pipe, 2 digit split
+    by tcgen05.mma), else the untuned default (the digit split from 8 columns
+    per pass)."""
+    if pinned != "auto":
+        return {"warp": 0, "fp32": 1, "tcgen05": 2}[pinned]
     import json
     import tempfile
     with tempfile.NamedTemporaryFile(suffix=".json") as f:
@@ -933,9 +938,12 @@ def bench_ours(args, w):
     cpl = dict(roofs["coupling"])
     traffic = None
     if prec == sm.SMASH_PREC_F32X2 and args.workload == "3d_invr_1m":
-        tr = OZ_COUPLING_TRAFFIC if _coupling_choice(sm, nrhs) == 0 else DD_COUPLING_TRAFFIC
+        choice = _coupling_choice(sm, nrhs, args.coupling)
+        tr = {0: OZ_COUPLING_TRAFFIC, 1: DD_COUPLING_TRAFFIC, 2: OZ5_COUPLING_TRAFFIC}[choice]
         traffic = tr[0] * info["coupling_pairs"] / tr[1]
-    roofline = {"bound": "alu", "kernel": "coupling over L (3.19)", "achieved": cpl["achieved"],
+        cpl["variant"] = COUPLING_NAMES[choice]
+    roofline = {"bound": "alu", "kernel": "coupling over L (3.19)" + (f", {cpl['variant']}" if "variant" in cpl else ""),
+                "achieved": cpl["achieved"],
                 "peak": cpl["peak"], "unit": "TFLOP/s", "frac": cpl["frac"], "traffic": traffic,
                 "traffic_source": None if traffic is None else
                 "ncu dram__bytes_read+write of the N=2^18 launch, scaled by kernel entries",

@@ -31,6 +31,14 @@ def test_recorded_choice_wins():
     assert bench._coupling_choice(sm, 4) == 0
 
 
+def test_pinned_coupling_wins_over_the_table():
+    sm = _FakeSm({"coupling_dd/sm152/k1/d3/ld16/n65536": 0})
+    assert bench._coupling_choice(sm, 16, "tcgen05") == 2
+    assert bench._coupling_choice(sm, 16, "fp32") == 1
+    assert bench._coupling_choice(sm, 16, "warp") == 0
+    assert bench._coupling_choice(sm, 16, "auto") == 0
+
+
 def test_untuned_default_follows_the_column_count():
     sm = _FakeSm({"compress/sm152/d3/p4/m512/n4096": 256})
     assert bench._coupling_choice(sm, 16) == 0
