@@ -48,7 +48,11 @@ typedef enum {
     SMASH_EINVAL = 1,   /* invalid argument */
     SMASH_ENOMEM = 2,   /* device or host allocation failed */
     SMASH_ECUDA = 3,    /* a CUDA runtime error (message has the detail) */
-    SMASH_ETIMEOUT = 4, /* a bounded device wait ran out */
+    SMASH_ETIMEOUT = 4, /* a bounded device wait ran out (the tcgen05 kernels wait on
+                           their MMA commits with an iteration limit).  The next
+                           synchronous matvec reports it and clears it; until then the
+                           tcgen05 digit-split coupling skips its work, so results of
+                           calls on caller streams in between are not valid */
     SMASH_EDEPTH = 5,   /* tree depth limit exceeded */
     SMASH_ENOTSUP = 6   /* option not supported on this device */
 } smash_status;
