@@ -178,6 +178,25 @@ __device__ __forceinline__ void oz_cp_wait_all() { asm volatile("cp.async.wait_a
 // round to the nearest integer (|x| < 2^22) by the 1.5 * 2^23 shift
 constexpr float kOzShift = 12582912.0f;
 
+// digit s of an entry kh + kl in its row's frame (sc0 = 2^(8 - E)): the first
+// three from kh, the fourth from the remainder r and kl (at 2^24 times the
+// first digit's weight), the last two from r; r carries the remainder, exact
+__device__ __forceinline__ float oz_digit(int s, float kh, float kl, float sc0, float &r) {
+    float dg;
+    if (s == 0) {
+        dg = fmaf(kh, sc0, kOzShift) - kOzShift;
+        r = fmaf(kh, sc0, -dg);
+    } else if (s == 3) {
+        const float x = fmaf(r, 256.0f, kl * (sc0 * 16777216.0f));
+        dg = (x + kOzShift) - kOzShift;
+        r = x - dg;
+    } else {
+        dg = fmaf(r, 256.0f, kOzShift) - kOzShift;
+        r = fmaf(r, 256.0f, -dg);
+    }
+    return dg;
+}
+
 // ------------------------------------------------------------------ coupling kernel
 struct KsumOzArgs {
     const int32_t *tnodes;
@@ -615,19 +634,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                         for (int s = 0; s < kOzDigits; ++s) {
                             float dg[4];
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                if (s == 0) {
-                                    dg[v] = fmaf(kh[v], sc0, kOzShift) - kOzShift;
-                                    r[v] = fmaf(kh[v], sc0, -dg[v]);
-                                } else if (s == 3) {
-                                    const float x = fmaf(r[v], 256.0f, kl[v] * (sc0 * 16777216.0f));
-                                    dg[v] = (x + kOzShift) - kOzShift;
-                                    r[v] = x - dg[v];
-                                } else {
-                                    dg[v] = fmaf(r[v], 256.0f, kOzShift) - kOzShift;
-                                    r[v] = fmaf(r[v], 256.0f, -dg[v]);
-                                }
-                            }
+                            for (int v = 0; v < 4; ++v) dg[v] = oz_digit(s, kh[v], kl[v], sc0, r[v]);
                             const uint32_t b0 = oz_pack(dg[0], dg[1]), b1 = oz_pack(dg[2], dg[3]);
 #pragma unroll
                             for (int t = 0; t + s < kOzDigits; ++t)
@@ -1018,19 +1025,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz5_kernel(KsumOzArgs a) {
                         for (int s = 0; s < kOzDigits; ++s) {
                             float dg[2];
 #pragma unroll
-                            for (int u = 0; u < 2; ++u) {
-                                if (s == 0) {
-                                    dg[u] = fmaf(kh[u], sc0, kOzShift) - kOzShift;
-                                    r[u] = fmaf(kh[u], sc0, -dg[u]);
-                                } else if (s == 3) {
-                                    const float x = fmaf(r[u], 256.0f, kl[u] * (sc0 * 16777216.0f));
-                                    dg[u] = (x + kOzShift) - kOzShift;
-                                    r[u] = x - dg[u];
-                                } else {
-                                    dg[u] = fmaf(r[u], 256.0f, kOzShift) - kOzShift;
-                                    r[u] = fmaf(r[u], 256.0f, -dg[u]);
-                                }
-                            }
+                            for (int u = 0; u < 2; ++u) dg[u] = oz_digit(s, kh[u], kl[u], sc0, r[u]);
                             w[s][j] = oz_pack(dg[0], dg[1]);
                         }
                     }
