@@ -1111,31 +1111,64 @@ __global__ void nf_width_kernel(SvdArgs a, int64_t *__restrict__ width) {
     width[i] = n;
 }
 
-template <int NT>
+// cluster-wide barrier: release of this thread's writes (shared and global)
+// to the other CTAs of the cluster, acquire of theirs
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// C = 1: one CTA per node, persistent over the level's nodes, every per-node
+// array in shared memory.  C > 1: a cluster of C CTAs (C SMs) per node, for
+// levels with fewer nodes than SMs: the dot-product chains, the rotations,
+// the kernel entries and the row norms are spread over the cluster's
+// threads, the shared per-node arrays (dot products, norms) live in the
+// node's global slot, and cluster barriers (release/acquire) separate the
+// phases; loads of data another CTA wrote bypass L1.  The same operations in
+// the same order either way, so the same bits.
+template <int NT, int C>
 __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double *sig = reinterpret_cast<double *>(smraw);  // m_cap
-    // the rotations of a round: (c, s) and the rows (p, q); p = -1 for none
     const int np_cap = a.m_cap / 2 + 1;  // pairs of a round at most
-    double *rot_c = sig + a.m_cap, *rot_s = rot_c + np_cap;
-    double *dots = rot_s + np_cap;     // [3][np_cap]: alpha, beta, gamma of each pair
-    int *rot_p = reinterpret_cast<int *>(dots + 3 * np_cap), *rot_q = rot_p + np_cap;
+    double *sig_s = reinterpret_cast<double *>(smraw);  // m_cap
+    // the rotations of a round: (c, s) and the rows (p, q); p = -1 for none
+    double *rot_c = sig_s + a.m_cap, *rot_s = rot_c + np_cap;
+    double *dots_s = rot_s + np_cap;  // [3][np_cap]: alpha, beta, gamma of each pair (C = 1)
+    int *rot_p = reinterpret_cast<int *>(dots_s + 3 * np_cap), *rot_q = rot_p + np_cap;
+    // C > 1: the rows of this CTA's pairs of a round, 2 per pair, n_cap each
+    double *rowbuf = reinterpret_cast<double *>(rot_q + np_cap);  // 8-byte aligned: 2 np_cap ints
     __shared__ int rotated;
     __shared__ int s_sel;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double *B = a.work + (int64_t)blockIdx.x * a.slot_doubles;
+    unsigned rank = 0;
+    if (C > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int gt = (int)rank * NT + tid, gw = (int)rank * (NT / 32) + warp;  // thread / warp in the node's group
+    constexpr int GT = C * NT, GW = C * (NT / 32);
+    const int64_t cid = blockIdx.x / C;  // the group (CTA or cluster)
+    double *B = a.work + cid * a.slot_doubles;
     double *JT = B + a.a_doubles;
-    for (int64_t ni = blockIdx.x; ni < a.nl; ni += gridDim.x) {
+    // per-node arrays shared by the group: shared memory for one CTA, the
+    // node's slot for a cluster
+    double *dots = C == 1 ? dots_s : JT + (int64_t)a.m_cap * a.m_cap;
+    double *sig = C == 1 ? sig_s : dots + 3 * np_cap;  // m_cap (sig[0] first holds ||A||_F^2)
+    auto ld = [](const double *p) {
+        if constexpr (C == 1) return *p;
+        else return __ldcg(p);
+    };
+    auto node_sync = [] {
+        if constexpr (C == 1) __syncthreads();
+        else cluster_sync_all();
+    };
+    for (int64_t ni = cid; ni < a.nl; ni += (C == 1 ? (int64_t)gridDim.x : a.nl)) {
         const int64_t g = a.n0 + ni;
         const int m = a.m_s[g];
         int n = 0;
         for (int64_t e = a.nf_ptr[g]; e < a.nf_ptr[g + 1]; ++e) n += ws_other_size(a, a.nf_col[e]);
         if (m == 0 || n == 0) {
-            if (tid == 0) a.s_out[g] = 0;
+            if (gt == 0) a.s_out[g] = 0;
             continue;
         }
         // A: rows = the node's working set, columns = the working sets of N_g
-        for (int col = tid; col < n; col += NT) {
+        for (int col = gt; col < n; col += GT) {
             int64_t e = a.nf_ptr[g];
             int base = 0, w = ws_other_size(a, a.nf_col[e]);
             while (col >= base + w) { base += w; ++e; w = ws_other_size(a, a.nf_col[e]); }
@@ -1146,16 +1179,19 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
                 B[(int64_t)r * n + col] = a.side == 0 ? kappa_1d(a.kid, xs, yo) : kappa_1d(a.kid, yo, xs);
             }
         }
-        for (int e = tid; e < m * m; e += NT) JT[e] = (e / m == e % m) ? 1.0 : 0.0;
-        __syncthreads();
-        if (tid == 0) {  // ||A||_F^2 in the oracle's (row-major) order: it sets the rotation floor
+        for (int e = gt; e < m * m; e += GT) JT[e] = (e / m == e % m) ? 1.0 : 0.0;
+        node_sync();
+        if (gt == 0) {  // ||A||_F^2 in the oracle's (row-major) order: it sets the rotation floor
             double f2 = 0.0;
-            for (int64_t e = 0; e < (int64_t)m * n; ++e) f2 = __fma_rn(B[e], B[e], f2);
+            for (int64_t e = 0; e < (int64_t)m * n; ++e) {
+                const double b = ld(B + e);
+                f2 = __fma_rn(b, b, f2);
+            }
             sig[0] = f2;
         }
-        __syncthreads();
-        const double floor_ab = kJacobiFloor * sig[0];
-        __syncthreads();
+        node_sync();
+        const double floor_ab = kJacobiFloor * ld(sig);
+        node_sync();
         const int M = m + (m & 1);
         for (int sweep = 0; sweep < kJacobiSweeps && m > 1; ++sweep) {
             if (tid == 0) rotated = 0;
@@ -1165,21 +1201,51 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
                 // sequential chain per thread in the oracle's order (a pair's
                 // three chains on neighbouring lanes of one warp)
                 const int np = M / 2;
-                for (int it = tid; it < 3 * np; it += NT) {
-                    const int i = it / 3, which = it - 3 * i;
-                    int pa, pb;
-                    if (i == 0) { pa = M - 1; pb = rr; }
-                    else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
-                    const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
-                    if (q >= m) continue;
-                    const double *bu = B + (int64_t)(which == 1 ? q : p) * n;
-                    const double *bv = B + (int64_t)(which == 0 ? p : q) * n;
-                    double acc = 0.0;
-                    for (int e = 0; e < n; ++e) acc = __fma_rn(bu[e], bv[e], acc);
-                    dots[which * np_cap + i] = acc;
+                if constexpr (C == 1) {
+                    for (int it = tid; it < 3 * np; it += NT) {
+                        const int i = it / 3, which = it - 3 * i;
+                        int pa, pb;
+                        if (i == 0) { pa = M - 1; pb = rr; }
+                        else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
+                        const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
+                        if (q >= m) continue;
+                        const double *bu = B + (int64_t)(which == 1 ? q : p) * n;
+                        const double *bv = B + (int64_t)(which == 0 ? p : q) * n;
+                        double acc = 0.0;
+                        for (int e = 0; e < n; ++e) acc = __fma_rn(bu[e], bv[e], acc);
+                        dots[which * np_cap + i] = acc;
+                    }
+                } else {
+                    // pair i to CTA i % C; its two rows are first copied from the
+                    // node's slot into shared memory by all the CTA's threads
+                    // (coalesced, from L2), then each chain runs from there
+                    const int npl = (np - (int)rank + C - 1) / C;  // this CTA's pairs
+                    for (int idx = tid; idx < 2 * npl * n; idx += NT) {
+                        const int r2 = idx / n, e = idx - r2 * n;
+                        const int i = (r2 >> 1) * C + (int)rank;
+                        int pa, pb;
+                        if (i == 0) { pa = M - 1; pb = rr; }
+                        else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
+                        const int row = (r2 & 1) ? (pa < pb ? pb : pa) : (pa < pb ? pa : pb);
+                        if (row < m) rowbuf[(int64_t)r2 * n + e] = __ldcg(B + (int64_t)row * n + e);
+                    }
+                    __syncthreads();
+                    for (int it = tid; it < 3 * npl; it += NT) {
+                        const int li = it / 3, which = it - 3 * li, i = li * C + (int)rank;
+                        int pa, pb;
+                        if (i == 0) { pa = M - 1; pb = rr; }
+                        else { pa = (rr + i) % (M - 1); pb = (rr - i + (M - 1)) % (M - 1); }
+                        if ((pa < pb ? pb : pa) >= m) continue;
+                        const double *bu = rowbuf + (int64_t)(2 * li + (which == 1 ? 1 : 0)) * n;
+                        const double *bv = rowbuf + (int64_t)(2 * li + (which == 0 ? 0 : 1)) * n;
+                        double acc = 0.0;
+                        for (int e = 0; e < n; ++e) acc = __fma_rn(bu[e], bv[e], acc);
+                        dots[which * np_cap + i] = acc;
+                    }
                 }
-                __syncthreads();
-                // (1b) each pair's rotation
+                node_sync();
+                // (1b) each pair's rotation (every CTA of a cluster decides all
+                // of them, from the same dot products)
                 for (int i = tid; i < np; i += NT) {
                     int pa, pb;
                     if (i == 0) { pa = M - 1; pb = rr; }
@@ -1187,7 +1253,7 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
                     const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
                     rot_p[i] = -1;
                     if (q >= m) continue;
-                    const double al = dots[i], be = dots[np_cap + i], ga = dots[2 * np_cap + i];
+                    const double al = ld(dots + i), be = ld(dots + np_cap + i), ga = ld(dots + 2 * np_cap + i);
                     const double nab = sqrt(al) * sqrt(be);
                     if (ga == 0.0 || !(fabs(ga) > kJacobiEps * nab) || !(nab > floor_ab)) continue;
                     const double zeta = (be - al) / (2.0 * ga);
@@ -1202,50 +1268,98 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
                 __syncthreads();
                 // (2) the rotations, element by element over all threads (each
                 // element's two products and difference as in the oracle)
-                for (int i = warp; i < M / 2; i += NT / 32) {
+                for (int i = gw; i < np; i += GW) {
                     const int p = rot_p[i];
                     if (p < 0) continue;
                     const int q = rot_q[i];
                     const double c = rot_c[i], sn = rot_s[i];
                     double *bp = B + (int64_t)p * n, *bq = B + (int64_t)q * n;
-                    for (int e = lane; e < n; e += 32) {
-                        const double u = bp[e], v = bq[e];
-                        bp[e] = c * u - sn * v;
-                        bq[e] = sn * u + c * v;
-                    }
                     double *jp = JT + (int64_t)p * m, *jq = JT + (int64_t)q * m;
-                    for (int e = lane; e < m; e += 32) {
-                        const double u = jp[e], v = jq[e];
-                        jp[e] = c * u - sn * v;
-                        jq[e] = sn * u + c * v;
+                    if constexpr (C == 1) {
+                        for (int e = lane; e < n; e += 32) {
+                            const double u = bp[e], v = bq[e];
+                            bp[e] = c * u - sn * v;
+                            bq[e] = sn * u + c * v;
+                        }
+                        for (int e = lane; e < m; e += 32) {
+                            const double u = jp[e], v = jq[e];
+                            jp[e] = c * u - sn * v;
+                            jq[e] = sn * u + c * v;
+                        }
+                    } else {
+                        // from L2: a batch of loads in flight before its stores
+                        constexpr int kB = 8;
+                        for (int e0 = lane; e0 < n; e0 += 32 * kB) {
+                            double u[kB], v[kB];
+#pragma unroll
+                            for (int k = 0; k < kB; ++k) {
+                                const int e = e0 + 32 * k;
+                                u[k] = e < n ? __ldcg(bp + e) : 0.0;
+                                v[k] = e < n ? __ldcg(bq + e) : 0.0;
+                            }
+#pragma unroll
+                            for (int k = 0; k < kB; ++k) {
+                                const int e = e0 + 32 * k;
+                                if (e < n) {
+                                    bp[e] = c * u[k] - sn * v[k];
+                                    bq[e] = sn * u[k] + c * v[k];
+                                }
+                            }
+                        }
+                        for (int e0 = lane; e0 < m; e0 += 32 * kB) {
+                            double u[kB], v[kB];
+#pragma unroll
+                            for (int k = 0; k < kB; ++k) {
+                                const int e = e0 + 32 * k;
+                                u[k] = e < m ? __ldcg(jp + e) : 0.0;
+                                v[k] = e < m ? __ldcg(jq + e) : 0.0;
+                            }
+#pragma unroll
+                            for (int k = 0; k < kB; ++k) {
+                                const int e = e0 + 32 * k;
+                                if (e < m) {
+                                    jp[e] = c * u[k] - sn * v[k];
+                                    jq[e] = sn * u[k] + c * v[k];
+                                }
+                            }
+                        }
                     }
                 }
-                __syncthreads();
+                node_sync();
             }
             const bool any = rotated != 0;
             __syncthreads();
             if (!any) break;
         }
-        for (int p = tid; p < m; p += NT) {
+        for (int p = gt; p < m; p += GT) {
             double s2 = 0.0;
-            for (int e = 0; e < n; ++e) s2 = __fma_rn(B[(int64_t)p * n + e], B[(int64_t)p * n + e], s2);
+            for (int e = 0; e < n; ++e) {
+                const double b = ld(B + (int64_t)p * n + e);
+                s2 = __fma_rn(b, b, s2);
+            }
             sig[p] = sqrt(s2);
         }
-        __syncthreads();
+        node_sync();
+        // the rest on one CTA (rank 0 of a cluster; no cluster barrier follows)
+        if (rank != 0) continue;
+        if (C > 1) {
+            for (int p = tid; p < m; p += NT) sig_s[p] = ld(sig + p);
+            __syncthreads();
+        }
         // keep the singular values above eps_svd of the largest, descending
         // (ties: the lower row first); sig of a kept row is set to -1
         double *dst = a.ST + ni * a.st_stride;
         if (tid == 0) {
             double smax = 0.0;
-            for (int p = 0; p < m; ++p) if (sig[p] > smax) smax = sig[p];
+            for (int p = 0; p < m; ++p) if (sig_s[p] > smax) smax = sig_s[p];
             int sc = 0;
             for (;;) {
                 int best = -1;
                 for (int p = 0; p < m; ++p)
-                    if (sig[p] >= 0.0 && (best < 0 || sig[p] > sig[best])) best = p;
-                if (best < 0 || !(sig[best] > a.eps_svd * smax) || !(sig[best] > 0.0)) break;
+                    if (sig_s[p] >= 0.0 && (best < 0 || sig_s[p] > sig_s[best])) best = p;
+                if (best < 0 || !(sig_s[best] > a.eps_svd * smax) || !(sig_s[best] > 0.0)) break;
                 if (sc == kHssSvdCap) { *a.overflow = 1; break; }
-                sig[best] = -1.0 - (double)sc;  // kept, in this order
+                sig_s[best] = -1.0 - (double)sc;  // kept, in this order
                 ++sc;
             }
             s_sel = sc;
@@ -1253,10 +1367,10 @@ __global__ void __launch_bounds__(NT) nearfield_svd_kernel(SvdArgs a) {
         __syncthreads();
         const int sc = s_sel;
         for (int p = 0; p < m; ++p) {
-            const double v = sig[p];
+            const double v = sig_s[p];
             if (v >= 0.0) continue;
             const int t = (int)(-v - 1.0);
-            for (int e = tid; e < m; e += NT) dst[(int64_t)t * m + e] = JT[(int64_t)p * m + e];
+            for (int e = tid; e < m; e += NT) dst[(int64_t)t * m + e] = ld(JT + (int64_t)p * m + e);
         }
         if (tid == 0) a.s_out[g] = sc;
         __syncthreads();
@@ -1412,20 +1526,54 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             stbuf[i] = scratch.alloc<double>((size_t)nl * v.st_stride);
             v.ST = stbuf[i];
             // eight warps per node: a round's dot-product chains (three per
-            // pair) fill them; slots of at most 256 MiB in all, at least one CTA
-            // per SM
+            // pair) fill them.  Levels with few nodes give each node a cluster
+            // of C CTAs (C SMs; up to 4 CTAs per SM in all); the others run one
+            // CTA per node, persistent, slots of at most 256 MiB in all and at
+            // least one CTA per SM
             constexpr int NT = 256;
-            const int64_t fit = std::max<int64_t>(1, (int64_t)(256ll << 20) / (v.slot_doubles * 8));
-            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nl, std::max<int64_t>(
-                                                                                std::min<int64_t>(fit, 4 * h->num_sms),
-                                                                                h->num_sms)));
-            double *slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
-            v.work = slots;
             v.m_cap = (int)m_cap;
-            const size_t smem = sizeof(double) * (size_t)m_cap + (5 * sizeof(double) + 2 * sizeof(int)) *
-                                                                    (size_t)(m_cap / 2 + 1);
-            allow_max_dynamic_smem((const void *)nearfield_svd_kernel<NT>);
-            nearfield_svd_kernel<NT><<<(unsigned)grid, NT, smem, st>>>(v);
+            const int64_t np_cap = m_cap / 2 + 1;
+            size_t smem = sizeof(double) * (size_t)m_cap + (5 * sizeof(double) + 2 * sizeof(int)) * (size_t)np_cap;
+            const int64_t room = 4 * (int64_t)h->num_sms;
+            // (measured: clusters pay on the top levels only; at 128 or more
+            // nodes one CTA per node does better)
+            int C = nl <= 64 ? 8 : 1;
+            // a cluster CTA also holds the rows of its pairs (2 per pair)
+            auto rows_bytes = [&](int c) { return sizeof(double) * 2 * (size_t)((np_cap + c - 1) / c) * (size_t)n_cap; };
+            while (C > 1 && smem + rows_bytes(C) > (size_t)200 * 1024) C /= 2;
+            if (C > 1) smem += rows_bytes(C);
+            double *slots = nullptr;
+            if (C == 1) {
+                const int64_t fit = std::max<int64_t>(1, (int64_t)(256ll << 20) / (v.slot_doubles * 8));
+                const int64_t grid = std::max<int64_t>(
+                    1, std::min<int64_t>(nl, std::max<int64_t>(std::min<int64_t>(fit, room), h->num_sms)));
+                slots = scratch.alloc<double>((size_t)grid * v.slot_doubles);
+                v.work = slots;
+                allow_max_dynamic_smem((const void *)nearfield_svd_kernel<NT, 1>);
+                nearfield_svd_kernel<NT, 1><<<(unsigned)grid, NT, smem, st>>>(v);
+            } else {
+                // one slot per node: B, JT, then the dot products and row norms
+                // that the cluster shares
+                v.slot_doubles += 3 * (m_cap / 2 + 1) + m_cap;
+                slots = scratch.alloc<double>((size_t)nl * v.slot_doubles);
+                v.work = slots;
+                void (*kern)(SvdArgs) = C == 8 ? nearfield_svd_kernel<NT, 8>
+                                               : (C == 4 ? nearfield_svd_kernel<NT, 4> : nearfield_svd_kernel<NT, 2>);
+                allow_max_dynamic_smem((const void *)kern);
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(nl * C));
+                cfg.blockDim = dim3(NT);
+                cfg.dynamicSmemBytes = smem;
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)C;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                CK(cudaLaunchKernelEx(&cfg, kern, v));
+            }
             LAUNCHED();
             scratch.free(slots);
         }
