@@ -1526,10 +1526,10 @@ void build_compression_hss(smash_h2 *h, Arena &scratch) {
             stbuf[i] = scratch.alloc<double>((size_t)nl * v.st_stride);
             v.ST = stbuf[i];
             // eight warps per node: a round's dot-product chains (three per
-            // pair) fill them.  Levels with few nodes give each node a cluster
-            // of C CTAs (C SMs; up to 4 CTAs per SM in all); the others run one
-            // CTA per node, persistent, slots of at most 256 MiB in all and at
-            // least one CTA per SM
+            // pair) fill them.  Levels of at most 64 nodes give each node a
+            // cluster of 8 CTAs (8 SMs); the others run one CTA per node,
+            // persistent, slots of at most 256 MiB in all and at least one CTA
+            // per SM
             constexpr int NT = 256;
             v.m_cap = (int)m_cap;
             const int64_t np_cap = m_cap / 2 + 1;
