@@ -101,6 +101,16 @@ def test_full_size_headline_workload_f32x2(headline_oracle):
     zo, sc = oracle_reference(ho, q, pick)
     rows = leaf_rows(eo, pick)
     assert_entrywise(z2, zo, sc, TOL_F32X2, rows=rows, what="N=2^20 sampled leaves")
+    # the same with the coupling pinned to its tcgen05 form (a tuning
+    # candidate the headline does not take by default)
+    try:
+        sm.smash_autotune_force("coupling_dd/", 2)
+        z5 = H.matvec(_dev(q), precision=F32X2).cpu().numpy()
+    finally:
+        sm.smash_autotune_force("coupling_dd/", -1)
+    assert_entrywise(z5, zo, sc, TOL_F32X2, rows=rows, what="N=2^20 sampled leaves, tcgen05 coupling")
+    assert _rel(z5, z64) <= RTOL
+    assert _rel(z5, z2) <= 1e-12
     H.close()
 
 
