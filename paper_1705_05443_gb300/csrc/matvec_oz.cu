@@ -302,6 +302,70 @@ __device__ __forceinline__ float oz_point_gap2(const float4 &x, const KsumOzArgs
     return best;
 }
 
+// Near field: the nearest source of target point x (hi parts; the target's
+// own point excluded) and an upper bound of the farthest, over the partners
+// of its leaf g.  The leaf's own points are scanned first (the four lanes of
+// a quad split them); a partner leaf is scanned (by one lane) only if the
+// lower bound of r^2 from its cell box does not exceed the nearest found so
+// far, so the minimum is the same as over all sources: every value the FP32
+// r^2 of a skipped point could take lies above the bound (gaps reduced by
+// 2^-22 for the hi parts' rounding, the sum by 2^-20 relative).  The
+// farthest is bounded from the boxes (gaps grown by 2^-22, 2^-20 relative).
+template <int D>
+__device__ __forceinline__ void oz_near_extremes(const float4 &x, const KsumOzArgs &a, int64_t g, int64_t e0,
+                                                 int64_t e1, int t4, int64_t self, float &dmin2, float &dmax2) {
+    const float xv[3] = {x.x, x.y, x.z};
+    auto r2_of = [&](int64_t src) {
+        const float4 y = __ldg(reinterpret_cast<const float4 *>(a.ys + src * 8));
+        const float dx = x.x - y.x, dy = D > 1 ? x.y - y.y : 0.f, dz = D > 2 ? x.z - y.z : 0.f;
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    };
+    float best = INFINITY, far = 0.f;
+    {
+        const int64_t so = a.s_off[g];
+        const int cnt = a.s_cnt[g];
+        for (int b = t4; b < cnt; b += 4) {
+            if (so + b == self) continue;
+            const float r2 = r2_of(so + b);
+            best = fminf(best, r2);
+            far = fmaxf(far, r2);
+        }
+    }
+    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 1));
+    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 2));
+    for (int64_t e = e0 + t4; e < e1; e += 4) {
+        const int64_t j = a.col[e];
+        if (j == g) continue;
+        const float w = ldexpf(1.0f, 1 - a.level[j]);  // cell width (the root is level 1)
+        const uint64_t *cj = a.cell + j * 3;
+        float lb = 0.f, ub = 0.f;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const float lo = fmaf((float)cj[ax], w, 1.0f);  // exact: c < 2^9, w a power of two
+            const float below = lo - xv[ax], above = xv[ax] - (lo + w);
+            const float gap = fmaxf(fmaxf(below, above) - 0x1p-22f, 0.f);
+            const float span = fmaxf(-below, -above) + 0x1p-22f;  // to the far face
+            lb = fmaf(gap, gap, lb);
+            ub = fmaf(span, span, ub);
+        }
+        far = fmaxf(far, ub * (1.0f + 0x1p-20f));
+        if (lb * (1.0f - 0x1p-20f) > best) continue;
+        const int64_t so = a.s_off[j];
+        const int cnt = a.s_cnt[j];
+        for (int b = 0; b < cnt; ++b) {
+            if (so + b == self) continue;
+            best = fminf(best, r2_of(so + b));
+        }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        far = fmaxf(far, __shfl_xor_sync(0xffffffffu, far, o));
+    }
+    dmin2 = best;
+    dmax2 = far;
+}
+
 // exponent E with K' = K 2^-E in (-1/2, 1/2) for every entry of the row of x
 __device__ __forceinline__ int oz_row_exponent(float gap2, double node_kb) {
     float kb = (float)(node_kb * (1.0 + 1e-6));
@@ -483,50 +547,21 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                 //
                 // Every (target, source) pair is visited once: the warps of a
                 // target tile and the lanes of a quad split each staged tile.
-                const int64_t self = a.same ? tpt : -1;
-                float dmin2 = INFINITY, dmax2 = 0.f;
-                if (tid < kOzRows) {
-                    s_dmin[tid] = __float_as_uint(INFINITY);
-                    s_dmax[tid] = 0u;
-                }
-                for (int64_t e = e0; e < e1;) {
-                    load_partner_chunk<kOzThreads>(pc, e, e1, a.col, a.s_off, a.s_cnt);
-                    const int total = pc.pre[pc.n];
-                    e += pc.n;
-                    for (int pos = 0; pos < total; pos += CAP) {
-                        const int fill = min(CAP, total - pos);
-                        for (int q = tid; q < fill; q += kOzThreads) {
-                            const int64_t src = chunk_source(pc, pos + q);
-                            sidx[q] = src;
-                            sy[q] = *reinterpret_cast<const float4 *>(a.ys + src * 8);
-                        }
-                        __syncthreads();
-                        if (active)
-                            for (int b = grp * 4 + t4; b < fill; b += 4 * groups) {
-                                if (sidx[b] == self) continue;
-                                const float4 y = sy[b];
-                                const float dx = xh.x - y.x, dy = D > 1 ? xh.y - y.y : 0.f,
-                                            dz = D > 2 ? xh.z - y.z : 0.f;
-                                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                                dmin2 = fminf(dmin2, r2);
-                                dmax2 = fmaxf(dmax2, r2);
-                            }
-                        __syncthreads();
+                // one quad per target row of the pass
+                {
+                    const int q = tid >> 2;
+                    const int64_t qpt = toff + tb + (q < tcount ? q : 0);
+                    const float4 qx = *reinterpret_cast<const float4 *>(a.xt + qpt * 8);
+                    float mn, mx;
+                    oz_near_extremes<D>(qx, a, g, e0, e1, t4, a.same ? qpt : -1, mn, mx);
+                    if (t4 == 0 && q < kOzRows) {
+                        s_dmin[q] = __float_as_uint(mn);
+                        s_dmax[q] = __float_as_uint(mx);
                     }
                 }
-#pragma unroll
-                for (int o = 1; o <= 2; o <<= 1) {
-                    dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o));
-                    dmax2 = fmaxf(dmax2, __shfl_xor_sync(0xffffffffu, dmax2, o));
-                }
-                // non-negative floats order as their bit patterns
-                if (active && t4 == 0) {
-                    atomicMin(&s_dmin[tr], __float_as_uint(dmin2));
-                    atomicMax(&s_dmax[tr], __float_as_uint(dmax2));
-                }
                 __syncthreads();
-                dmin2 = __uint_as_float(s_dmin[tr]);
-                dmax2 = __uint_as_float(s_dmax[tr]);
+                float dmin2 = __uint_as_float(s_dmin[tr]);
+                float dmax2 = __uint_as_float(s_dmax[tr]);
                 const float dlo = sqrtf(dmin2) * (1.0f - 0x1p-20f) - 0x1p-22f;
                 const bool bad = !(dlo > 0.f) || dmax2 > 0x1p24f * dmin2;
                 E = bad ? 0 : ilogbf((1.0f / dlo) * (1.0f + 0x1p-18f)) + 2;
