@@ -221,6 +221,7 @@ struct KsumOzArgs {
     float n3h, n3l;            // 2^e / s as a two-float: exact-frame differences times it are normalised
     int *fallback;             // per CTA: 1 when the node is left to the double-float kernel
     int same;                  // X = Y: a target meets its own point (entry 0)
+    int boxes;                 // one tree: cell boxes bound the normalised coordinates
 };
 
 // digit bytes per source in shared memory: 6 * NC bf16 plus 16 bytes of pad,
@@ -305,7 +306,8 @@ __device__ __forceinline__ float oz_point_gap2(const float4 &x, const KsumOzArgs
 // Near field: the nearest source of target point x (hi parts; the target's
 // own point excluded) and an upper bound of the farthest, over the partners
 // of its leaf g.  The leaf's own points are scanned first (the four lanes of
-// a quad split them); a partner leaf is scanned (by one lane) only if the
+// a quad split them); for one tree (a batch of trees scans every partner) a
+// partner leaf is scanned (by one lane) only if the
 // lower bound of r^2 from its cell box does not exceed the nearest found so
 // far, so the minimum is the same as over all sources: every value the FP32
 // r^2 of a skipped point could take lies above the bound (gaps reduced by
@@ -336,6 +338,17 @@ __device__ __forceinline__ void oz_near_extremes(const float4 &x, const KsumOzAr
     for (int64_t e = e0 + t4; e < e1; e += 4) {
         const int64_t j = a.col[e];
         if (j == g) continue;
+        const int64_t so = a.s_off[j];
+        const int cnt = a.s_cnt[j];
+        if (!a.boxes) {  // a batch of trees: cells are not in the normalised frame, scan all
+            for (int b = 0; b < cnt; ++b) {
+                if (so + b == self) continue;
+                const float r2 = r2_of(so + b);
+                best = fminf(best, r2);
+                far = fmaxf(far, r2);
+            }
+            continue;
+        }
         const float w = ldexpf(1.0f, 1 - a.level[j]);  // cell width (the root is level 1)
         const uint64_t *cj = a.cell + j * 3;
         float lb = 0.f, ub = 0.f;
@@ -350,8 +363,6 @@ __device__ __forceinline__ void oz_near_extremes(const float4 &x, const KsumOzAr
         }
         far = fmaxf(far, ub * (1.0f + 0x1p-20f));
         if (lb * (1.0f - 0x1p-20f) > best) continue;
-        const int64_t so = a.s_off[j];
-        const int cnt = a.s_cnt[j];
         for (int b = 0; b < cnt; ++b) {
             if (so + b == self) continue;
             best = fminf(best, r2_of(so + b));
@@ -547,16 +558,25 @@ __global__ void __launch_bounds__(kOzThreads, 3) ksum_oz_kernel(KsumOzArgs a) {
                 //
                 // Every (target, source) pair is visited once: the warps of a
                 // target tile and the lanes of a quad split each staged tile.
-                // one quad per target row of the pass
+                // one quad per target row of the pass (warps past the rows sit
+                // out); rows past tcount, which the MMA tiles pad with target 0,
+                // take row 0's values
                 {
                     const int q = tid >> 2;
-                    const int64_t qpt = toff + tb + (q < tcount ? q : 0);
-                    const float4 qx = *reinterpret_cast<const float4 *>(a.xt + qpt * 8);
-                    float mn, mx;
-                    oz_near_extremes<D>(qx, a, g, e0, e1, t4, a.same ? qpt : -1, mn, mx);
-                    if (t4 == 0 && q < kOzRows) {
-                        s_dmin[q] = __float_as_uint(mn);
-                        s_dmax[q] = __float_as_uint(mx);
+                    if (warp * 8 < tcount) {
+                        const int64_t qpt = toff + tb + (q < tcount ? q : 0);
+                        const float4 qx = *reinterpret_cast<const float4 *>(a.xt + qpt * 8);
+                        float mn, mx;
+                        oz_near_extremes<D>(qx, a, g, e0, e1, t4, a.same ? qpt : -1, mn, mx);
+                        if (t4 == 0 && q < tcount) {
+                            s_dmin[q] = __float_as_uint(mn);
+                            s_dmax[q] = __float_as_uint(mx);
+                        }
+                    }
+                    __syncthreads();
+                    if (tid < kOzRows && tid >= tcount) {
+                        s_dmin[tid] = s_dmin[0];
+                        s_dmax[tid] = s_dmax[0];
                     }
                 }
                 __syncthreads();
@@ -1316,7 +1336,7 @@ void near_oz(const smash_h2 *h, int kid, const double *qs, double *zs, int ldq, 
         a.n3h = (float)nrm;
         a.n3l = (float)(nrm - (double)a.n3h);
     }
-    a.fallback = fallback; a.same = h->same;
+    a.fallback = fallback; a.same = h->same; a.boxes = h->nroots == 1;
     launch_oz_kernel<true>(h, kid, a, h->nleaves, s);
     tmp.release();
 }
